@@ -1,0 +1,200 @@
+/*
+ * cpm.h -- C ABI of libcpm: the GB300 (sm_103a) hot path of the closest point
+ * method (CPM) solver for the shifted surface Poisson problem
+ *
+ *     (c - Delta_S) u = f                                   (Section 1, eq. shiftPoisson)
+ *
+ * of May, Haynes & Ruuth, "A closest point method library for PDEs on surfaces
+ * with parallel domain decomposition solvers and preconditioners" (arXiv
+ * 2110.06322), discretised on a narrow band of a uniform grid (Section 2.1)
+ * and solved by GMRES preconditioned by restricted additive Schwarz with
+ * Dirichlet (RAS) or Robin (ORAS) transmission (Section 2.2, Section 4.1.1).
+ *
+ * Conventions shared by every call
+ *   - Vectors are CALLER-OWNED DEVICE pointers of length N_A (the number of
+ *     active band nodes), in the band's canonical order: lexicographic in the
+ *     lattice index (i, j, k), k fastest.  Lattice node (i, j, k) is the point
+ *     (i h, j h, k h).  Several right-hand sides are stored one after another
+ *     (rhs-major, N_A apart).
+ *   - Handles (cpm_band, oras_pc) are LIBRARY-OWNED; free them with the
+ *     matching *_free call.  They live on the device that was current when
+ *     they were built.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Every call
+ *     is ordered on it.  Only cpm_band_build, oras_setup and cpm_solve* wait
+ *     on the host (to size allocations and to fill the info struct).
+ *   - Errors are returned as cpm_status codes; a message for the last error
+ *     of the calling thread is available from cpm_last_error().  No call
+ *     aborts the process or traps the device.  Kernels that wait on a
+ *     condition bound their wait and report CPM_ERR_TIMEOUT.
+ */
+#ifndef CPM_H
+#define CPM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CPM_OK = 0,
+  CPM_ERR_ARG = 1,            /* invalid argument (null pointer, size, kind) */
+  CPM_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+  CPM_ERR_OOM = 3,            /* device allocation failed */
+  CPM_ERR_BAND = 4,           /* band not within the surface reach, or not closed */
+  CPM_ERR_NOT_CONVERGED = 5,  /* iteration limit reached before the tolerance */
+  CPM_ERR_BREAKDOWN = 6,      /* zero pivot in ILU(0) or Krylov breakdown */
+  CPM_ERR_NAN = 7,            /* NaN or Inf met in an input or a residual */
+  CPM_ERR_TIMEOUT = 8         /* a bounded device-side wait ran out */
+} cpm_status;
+
+typedef enum { CPM_F64 = 0, CPM_F32 = 1, CPM_BF16 = 2 } cpm_dtype;
+
+/* Surface (Section 2.1, closest point function eq. cpFunc).
+ *   kind 0: sphere,  param = {cx, cy, cz, rho}
+ *   kind 1: torus about the z axis through (cx, cy, cz), param = {cx, cy, cz, R, r}, R > r > 0 */
+typedef struct {
+  int32_t kind;
+  double param[8];
+} cpm_surface;
+
+typedef struct cpm_band cpm_band;
+typedef struct oras_pc oras_pc;
+
+/* ------------------------------------------------------------------ band
+ * cpm_band_build -- build the computational band (Section 2.1): the seed tube
+ * T = {x : dist(x, S) <= lambda}, lambda = h sqrt(2((p+1)/2)^2 + (1+(p+1)/2)^2)
+ * (sqrt(17) h for p = 3); the active set Sigma_A = union over x in T of the
+ * (p+1)^3 interpolation cube at cp(x), with base b = floor(cp/h - (p-1)/2);
+ * the ghost set Sigma_G = 6-neighbours of Sigma_A outside it; and one
+ * extension (E) row per node of Sigma_A and Sigma_G.
+ *   surf   host pointer to the surface;  h > 0;  p in {2, 3}.
+ *   out    receives the new handle (library-owned).
+ * Returns CPM_ERR_BAND when lambda >= the reach kappa^-1 (sphere rho, torus
+ * min(r, R - r)) or when some E-row cube leaves Sigma_A. */
+cpm_status cpm_band_build(const cpm_surface* surf, double h, int p, void* stream, cpm_band** out);
+
+/* Sizes of the band: |Sigma_A|, |Sigma_G|, |T|. Host pointers; any may be NULL. */
+cpm_status cpm_band_info(const cpm_band* band, int64_t* n_active, int64_t* n_ghost, int64_t* n_tube);
+
+/* Export the band to caller-owned DEVICE buffers (any may be NULL):
+ *   ijk_active [N_A x 3] int32, canonical order
+ *   ijk_ghost  [N_G x 3] int32, canonical order
+ *   erow_base  [N_C x 3] int32 and erow_cp [N_C x 3] double, N_C = N_A + N_G,
+ *              rows of Sigma_A (canonical) followed by rows of Sigma_G (canonical)
+ *   perm       [N_A] int64: position of canonical node q in the library's vectors
+ *              (the identity: vectors are stored in canonical order). */
+cpm_status cpm_band_export(const cpm_band* band, int32_t* ijk_active, int32_t* ijk_ghost, int32_t* erow_base,
+                           double* erow_cp, int64_t* perm, void* stream);
+
+/* Export the 1-D barycentric interpolation weights of every E row (Section
+ * 2.1, tensor-product barycentric Lagrange interpolation of degree p) to a
+ * caller-owned DEVICE buffer w1d [N_C x 3 x (p+1)] double, rows ordered as in
+ * cpm_band_export.  The tensor weight of cube node (u, v, w) is
+ * (w1d[r][0][u] * w1d[r][1][v]) * w1d[r][2][w]. */
+cpm_status cpm_band_weights(const cpm_band* band, double* w1d, void* stream);
+
+/* ------------------------------------------------------------------ operator
+ * cpm_apply -- y = M x (transpose = 0) or y = M^T x (transpose = 1), with
+ *   M = c I - Delta_S^h,  Delta_S^h = -(2d/h^2) I + (Delta^h + (2d/h^2) I) E
+ * (Section 2.1, eq. lapBel; d = 3): y_i = (c + 6/h^2) x_i - (1/h^2) sum over
+ * the six neighbours n of i of (E x)_n.  Matrix-free: each E row gathers its
+ * (p+1)^3 cube.
+ *   c      HOST array of nrhs shifts (c > 0 in the paper; any finite value accepted)
+ *   x, y   DEVICE buffers of nrhs x N_A elements of `dtype` (CPM_F64 or CPM_F32);
+ *          x and y must not overlap.
+ * The transposed apply gathers E^T through a precomputed transpose map (no
+ * atomics, deterministic). */
+cpm_status cpm_apply(const cpm_band* band, const double* c, const void* x, void* y, cpm_dtype dtype, int nrhs,
+                     int transpose, void* stream);
+
+/* ------------------------------------------------------------------ Schwarz preconditioner
+ * (Section 2.2; defaults of Section 4.1.1: alpha = 4, alpha_cross = 20, ILU(0) local solves)
+ *   nparts       number of disjoint subdomains N_S, from recursive coordinate
+ *                bisection of Sigma_A by lattice planes
+ *   overlap      N_O: layers of 6-adjacency within Sigma_A added to each part
+ *   robin        0: RAS (Dirichlet transmission); 1: ORAS with the Robin reading
+ *                A_j[i,i] += D_i / (1 + alpha h), D_i the sum of the entries of
+ *                row i of M dropped by the restriction (alpha_cross when those
+ *                columns belong to two or more other parts)
+ *   store        precision of the stored factors used by oras_apply with
+ *                CPM_F32 vectors: CPM_F32 or CPM_BF16 (FP64 factors are always kept) */
+typedef struct {
+  int32_t nparts;
+  int32_t overlap;
+  int32_t robin;
+  double alpha;
+  double alpha_cross;
+  int32_t store;
+} oras_params;
+
+/* oras_setup -- partition, overlap growth, local matrices A_j = R_j M R_j^T
+ * (+ Robin term), and ILU(0) of each A_j in its local order (descending
+ * distance to the surface, ties by canonical index).  c is the shift of M. */
+cpm_status oras_setup(const cpm_band* band, const oras_params* prm, double c, void* stream, oras_pc** out);
+
+/* oras_apply -- z = sum_j Rtilde_j^T (L_j U_j)^{-1} R_j r (transpose = 0) or
+ * z = sum_j R_j^T (L_j U_j)^{-T} Rtilde_j r (transpose = 1): restrict to the
+ * overlapping subdomains, solve with the ILU(0) factors, and keep each
+ * subdomain's values on its own disjoint part.  r, z: DEVICE, nrhs x N_A of
+ * dtype (CPM_F64 or CPM_F32), not overlapping. */
+cpm_status oras_apply(const oras_pc* pc, const void* r, void* z, cpm_dtype dtype, int nrhs, int transpose,
+                      void* stream);
+
+/* Sizes of the preconditioner: number of parts, sum of |S_j|, sum of nnz(A_j),
+ * and the largest number of forward-solve levels of any subdomain.  Host pointers. */
+cpm_status oras_info(const oras_pc* pc, int32_t* nparts, int64_t* total_rows, int64_t* total_nnz,
+                     int32_t* max_levels);
+
+/* Export the disjoint partition part[N_A] (int32) and the overlapping
+ * subdomains, concatenated in local order (int32 canonical node indices),
+ * with offsets sub_ptr[nparts + 1] (int64).  DEVICE buffers; any may be NULL. */
+cpm_status oras_export(const oras_pc* pc, int32_t* part, int64_t* sub_ptr, int32_t* sub_nodes, void* stream);
+
+/* ------------------------------------------------------------------ solver
+ * Restarted GMRES(restart), right preconditioned by the Schwarz preconditioner
+ * (Section 4.1.1: GMRES is the default Krylov method): classical Gram-Schmidt
+ * with an optional second pass (reorth), Givens least squares, stop when
+ * |f - M u|_2 <= rtol |f|_2 (true residual, FP64).
+ * mixed = 1: FP64 iterative refinement around an inner GMRES whose operator
+ * and preconditioner applies run in FP32 (factors stored per oras_params.store);
+ * the outer residual, Gram-Schmidt and the least-squares update stay FP64. */
+typedef struct {
+  int32_t restart;
+  int32_t maxit;      /* total inner GMRES iterations allowed */
+  double rtol;
+  int32_t mixed;
+  int32_t reorth;
+  double inner_rtol;  /* mixed only: relative tolerance of each inner solve */
+} cpm_solve_params;
+
+typedef struct {
+  int32_t iters;         /* GMRES iterations (inner iterations summed when mixed) */
+  int32_t restarts;      /* GMRES cycles */
+  int32_t ir_steps;      /* refinement steps (mixed) */
+  double rel_residual;   /* |f - M u|_2 / |f|_2 in FP64 at exit */
+  int32_t status;        /* cpm_status of the solve */
+} cpm_solve_info;
+
+/* cpm_solve -- solve M u = f.  f: DEVICE, N_A doubles.  u: DEVICE, N_A
+ * doubles, initial guess on entry, solution on exit.  pc may be NULL (no
+ * preconditioner).  info: HOST.  Synchronises the stream. */
+cpm_status cpm_solve(const cpm_band* band, const oras_pc* pc, double c, const double* f, double* u,
+                     const cpm_solve_params* prm, cpm_solve_info* info, void* stream);
+
+/* cpm_solve_adjoint -- solve M^T lambda = g with the transposed operator and
+ * the transposed preconditioner (same conventions as cpm_solve). */
+cpm_status cpm_solve_adjoint(const cpm_band* band, const oras_pc* pc, double c, const double* g, double* lambda,
+                             const cpm_solve_params* prm, cpm_solve_info* info, void* stream);
+
+void cpm_band_free(cpm_band* band);
+void oras_free(oras_pc* pc);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* cpm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CPM_H */

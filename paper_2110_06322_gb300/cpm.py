@@ -1,0 +1,249 @@
+"""Thin ctypes binding of libcpm (include/cpm.h).
+
+Argument marshalling only: every step runs in the CUDA library.  Functions
+carry the C names (cpm_band_build, cpm_apply, oras_setup, oras_apply,
+cpm_solve, cpm_solve_adjoint, ...); the classes Band and Schwarz own the
+handles.  Vectors are torch tensors on the CUDA device; the current torch
+stream is passed to every call unless a stream is given.
+
+There is no fallback: if libcpm.so is missing or no CUDA device is present,
+the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcpm.so")
+_lib = None
+
+CPM_OK, CPM_ERR_ARG, CPM_ERR_CUDA, CPM_ERR_OOM, CPM_ERR_BAND = 0, 1, 2, 3, 4
+CPM_ERR_NOT_CONVERGED, CPM_ERR_BREAKDOWN, CPM_ERR_NAN, CPM_ERR_TIMEOUT = 5, 6, 7, 8
+CPM_F64, CPM_F32, CPM_BF16 = 0, 1, 2
+STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_BAND", 5: "ERR_NOT_CONVERGED",
+                6: "ERR_BREAKDOWN", 7: "ERR_NAN", 8: "ERR_TIMEOUT"}
+
+
+class cpm_surface(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("param", C.c_double * 8)]
+
+
+class oras_params(C.Structure):
+    _fields_ = [("nparts", C.c_int32), ("overlap", C.c_int32), ("robin", C.c_int32), ("alpha", C.c_double),
+                ("alpha_cross", C.c_double), ("store", C.c_int32)]
+
+
+class cpm_solve_params(C.Structure):
+    _fields_ = [("restart", C.c_int32), ("maxit", C.c_int32), ("rtol", C.c_double), ("mixed", C.c_int32),
+                ("reorth", C.c_int32), ("inner_rtol", C.c_double)]
+
+
+class cpm_solve_info(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("restarts", C.c_int32), ("ir_steps", C.c_int32),
+                ("rel_residual", C.c_double), ("status", C.c_int32)]
+
+
+class CpmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def lib():
+    """Load libcpm.so (built in-tree by paper_2110_06322_gb300.build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2110_06322_gb300.build.build()")
+    L = C.CDLL(LIB_PATH)
+    vp, i32, i64, f64 = C.c_void_p, C.c_int, C.c_int64, C.c_double
+    P = C.POINTER
+    sig = {
+        "cpm_last_error": (C.c_char_p, []),
+        "cpm_band_build": (i32, [P(cpm_surface), f64, i32, vp, P(vp)]),
+        "cpm_band_info": (i32, [vp, P(C.c_int64), P(C.c_int64), P(C.c_int64)]),
+        "cpm_band_export": (i32, [vp, vp, vp, vp, vp, vp, vp]),
+        "cpm_band_weights": (i32, [vp, vp, vp]),
+        "cpm_apply": (i32, [vp, P(C.c_double), vp, vp, i32, i32, i32, vp]),
+        "oras_setup": (i32, [vp, P(oras_params), f64, vp, P(vp)]),
+        "oras_apply": (i32, [vp, vp, vp, i32, i32, i32, vp]),
+        "oras_info": (i32, [vp, P(C.c_int32), P(C.c_int64), P(C.c_int64), P(C.c_int32)]),
+        "oras_export": (i32, [vp, vp, vp, vp, vp]),
+        "cpm_solve": (i32, [vp, vp, f64, vp, vp, P(cpm_solve_params), P(cpm_solve_info), vp]),
+        "cpm_solve_adjoint": (i32, [vp, vp, f64, vp, vp, P(cpm_solve_params), P(cpm_solve_info), vp]),
+        "cpm_band_free": (None, [vp]),
+        "oras_free": (None, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+EXPORTED = ["cpm_last_error", "cpm_band_build", "cpm_band_info", "cpm_band_export", "cpm_band_weights", "cpm_apply",
+            "oras_setup", "oras_apply", "oras_info", "oras_export", "cpm_solve", "cpm_solve_adjoint", "cpm_band_free",
+            "oras_free"]
+
+
+def _check(st):
+    if st != CPM_OK:
+        raise CpmError(st, lib().cpm_last_error().decode())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _dtype_code(t):
+    if t.dtype == torch.float64:
+        return CPM_F64
+    if t.dtype == torch.float32:
+        return CPM_F32
+    raise TypeError("vectors must be float64 or float32 CUDA tensors")
+
+
+# ------------------------------------------------------------------ C names
+def cpm_band_build(kind, params, h, p=3, stream=None):
+    surf = cpm_surface()
+    surf.kind = int(kind)
+    for q, v in enumerate(params):
+        surf.param[q] = float(v)
+    out = C.c_void_p()
+    _check(lib().cpm_band_build(C.byref(surf), float(h), int(p), _stream(stream), C.byref(out)))
+    return out
+
+
+def cpm_apply(band, c, x, y, transpose=False, stream=None):
+    nrhs = x.numel() // Band.n_active_of(band)
+    cs = (C.c_double * nrhs)(*([float(c)] * nrhs if not hasattr(c, "__len__") else [float(v) for v in c]))
+    _check(lib().cpm_apply(band, cs, _ptr(x), _ptr(y), _dtype_code(x), nrhs, int(bool(transpose)), _stream(stream)))
+    return y
+
+
+def oras_setup(band, c, nparts, overlap, robin=False, alpha=4.0, alpha_cross=20.0, store=CPM_F32, stream=None):
+    prm = oras_params(int(nparts), int(overlap), int(bool(robin)), float(alpha), float(alpha_cross), int(store))
+    out = C.c_void_p()
+    _check(lib().oras_setup(band, C.byref(prm), float(c), _stream(stream), C.byref(out)))
+    return out
+
+
+def oras_apply(pc, r, z, n_active, transpose=False, stream=None):
+    nrhs = r.numel() // n_active
+    _check(lib().oras_apply(pc, _ptr(r), _ptr(z), _dtype_code(r), nrhs, int(bool(transpose)), _stream(stream)))
+    return z
+
+
+def cpm_solve(band, pc, c, f, u, restart=30, maxit=10000, rtol=1e-8, mixed=False, reorth=True, inner_rtol=1e-4,
+              adjoint=False, stream=None):
+    prm = cpm_solve_params(int(restart), int(maxit), float(rtol), int(bool(mixed)), int(bool(reorth)),
+                           float(inner_rtol))
+    info = cpm_solve_info()
+    fn = lib().cpm_solve_adjoint if adjoint else lib().cpm_solve
+    st = fn(band, pc, float(c), _ptr(f), _ptr(u), C.byref(prm), C.byref(info), _stream(stream))
+    if st not in (CPM_OK, CPM_ERR_NOT_CONVERGED):
+        _check(st)
+    return {"status": st, "iters": info.iters, "restarts": info.restarts, "ir_steps": info.ir_steps,
+            "rel_residual": info.rel_residual}
+
+
+def cpm_solve_adjoint(band, pc, c, g, lam, **kw):
+    return cpm_solve(band, pc, c, g, lam, adjoint=True, **kw)
+
+
+# ------------------------------------------------------------------ owning classes
+class Band:
+    """Computational band around a sphere (kind 0) or torus (kind 1)."""
+
+    _sizes = {}
+
+    def __init__(self, kind, params, h, p=3, stream=None):
+        self.kind, self.params, self.h, self.p = int(kind), tuple(params), float(h), int(p)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.handle = cpm_band_build(kind, params, h, p, stream)
+        nA, nG, nT = C.c_int64(), C.c_int64(), C.c_int64()
+        _check(lib().cpm_band_info(self.handle, C.byref(nA), C.byref(nG), C.byref(nT)))
+        self.n_active, self.n_ghost, self.n_tube = nA.value, nG.value, nT.value
+        self.n_rows = self.n_active + self.n_ghost
+        Band._sizes[self.handle.value] = self.n_active
+
+    @staticmethod
+    def n_active_of(handle):
+        return Band._sizes[handle.value]
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value and _lib is not None:
+            Band._sizes.pop(h.value, None)
+            _lib.cpm_band_free(h)
+            self.handle = None
+
+    def export(self, stream=None):
+        d = self.device
+        ijkA = torch.empty((self.n_active, 3), dtype=torch.int32, device=d)
+        ijkG = torch.empty((max(self.n_ghost, 1), 3), dtype=torch.int32, device=d)
+        base = torch.empty((self.n_rows, 3), dtype=torch.int32, device=d)
+        cp = torch.empty((self.n_rows, 3), dtype=torch.float64, device=d)
+        perm = torch.empty(self.n_active, dtype=torch.int64, device=d)
+        _check(lib().cpm_band_export(self.handle, _ptr(ijkA), _ptr(ijkG), _ptr(base), _ptr(cp), _ptr(perm),
+                                     _stream(stream)))
+        return ijkA, ijkG[: self.n_ghost], base, cp, perm
+
+    def weights(self, stream=None):
+        w = torch.empty((self.n_rows, 3, self.p + 1), dtype=torch.float64, device=self.device)
+        _check(lib().cpm_band_weights(self.handle, _ptr(w), _stream(stream)))
+        return w
+
+    def apply(self, c, x, transpose=False, out=None, stream=None):
+        y = torch.empty_like(x) if out is None else out
+        return cpm_apply(self.handle, c, x, y, transpose, stream)
+
+
+class Schwarz:
+    """(O)RAS preconditioner over a Band (Section 2.2)."""
+
+    def __init__(self, band, c, nparts, overlap, robin=False, alpha=4.0, alpha_cross=20.0, store=CPM_F32,
+                 stream=None):
+        self.band = band
+        self.c = float(c)
+        self.handle = oras_setup(band.handle, c, nparts, overlap, robin, alpha, alpha_cross, store, stream)
+        npt, rows, nnz, lev = C.c_int32(), C.c_int64(), C.c_int64(), C.c_int32()
+        _check(lib().oras_info(self.handle, C.byref(npt), C.byref(rows), C.byref(nnz), C.byref(lev)))
+        self.nparts, self.total_rows, self.total_nnz, self.max_levels = npt.value, rows.value, nnz.value, lev.value
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.oras_free(h)
+            self.handle = None
+
+    def apply(self, r, transpose=False, out=None, stream=None):
+        z = torch.empty_like(r) if out is None else out
+        return oras_apply(self.handle, r, z, self.band.n_active, transpose, stream)
+
+    def export(self, stream=None):
+        d = self.band.device
+        part = torch.empty(self.band.n_active, dtype=torch.int32, device=d)
+        sptr = torch.empty(self.nparts + 1, dtype=torch.int64, device=d)
+        nodes = torch.empty(max(self.total_rows, 1), dtype=torch.int32, device=d)
+        _check(lib().oras_export(self.handle, _ptr(part), _ptr(sptr), _ptr(nodes), _stream(stream)))
+        return part, sptr, nodes[: self.total_rows]
+
+
+def solve(band, f, pc=None, c=None, u0=None, adjoint=False, **kw):
+    """Solve M u = f (or M^T u = f) on the device; returns (u, info)."""
+    c = pc.c if c is None else float(c)
+    u = torch.zeros_like(f) if u0 is None else u0.clone()
+    info = cpm_solve(band.handle, pc.handle if pc is not None else None, c, f, u, adjoint=adjoint, **kw)
+    return u, info

@@ -1,0 +1,302 @@
+// apply.cu -- matrix-free CPM operator (Section 2.1, eq. lapBel):
+//
+//   y_i = (c + 6/h^2) x_i - (1/h^2) * sum_{n in N6(i)} (E x)_n
+//
+// Pass 1 (k_erow_apply) evaluates (E x)_r once for every row r of Sigma_A u
+// Sigma_G: a (p+1)^3 tensor-product interpolation, contracted axis by axis
+// (z, then y, then x).  The cube's nodes along k are consecutive in the
+// canonical order, so each (u, v) pencil costs one bitmap rank lookup.
+// Pass 2 (k_stencil) forms the 7-point stencil from those values; the +-k
+// neighbours of a row are the adjacent rows.
+//
+// The transposed apply uses y = (c + 6/h^2) x - (1/h^2) E^T (L_off^T x):
+// v_r = sum of x over the active neighbours of row r, then E^T v gathered
+// through a transpose map (for each active m, its (row, position) pairs in
+// ascending row order) -- no atomics, so the sum order is fixed.
+#include "kernels.cuh"
+
+namespace cpm {
+
+namespace {
+
+struct ApplyGeom {
+  Grid g;
+  const BitWord* amap;
+  const BitWord* rmap;
+  const int32_t* ijkA;
+  const int32_t* arow;
+  const int32_t* rbase;
+  const double* w1d;
+  const float* s32;
+  int64_t nA, nR;
+  double coef;  // 1/h^2
+};
+
+constexpr int MAXRHS = 16;
+struct Shifts {
+  double c[MAXRHS];
+};
+
+// Lagrange weights of nodes 0..P at s (product form; used for the FP32 apply)
+template <int P>
+__device__ __forceinline__ void lagrange_f32(float s, float* l) {
+#pragma unroll
+  for (int j = 0; j <= P; ++j) {
+    float num = 1.0f, den = 1.0f;
+#pragma unroll
+    for (int k = 0; k <= P; ++k)
+      if (k != j) {
+        num *= (s - (float)k);
+        den *= (float)(j - k);
+      }
+    l[j] = num / den;
+  }
+}
+
+template <typename T, int P>
+__device__ __forceinline__ void row_weights(const ApplyGeom& G, int64_t r, T (&l)[3][P + 1]);
+
+template <>
+__device__ __forceinline__ void row_weights<double, 3>(const ApplyGeom& G, int64_t r, double (&l)[3][4]) {
+  const double* w = G.w1d + r * 12;
+#pragma unroll
+  for (int q = 0; q < 12; ++q) l[q / 4][q % 4] = w[q];
+}
+template <>
+__device__ __forceinline__ void row_weights<double, 2>(const ApplyGeom& G, int64_t r, double (&l)[3][3]) {
+  const double* w = G.w1d + r * 9;
+#pragma unroll
+  for (int q = 0; q < 9; ++q) l[q / 3][q % 3] = w[q];
+}
+template <>
+__device__ __forceinline__ void row_weights<float, 3>(const ApplyGeom& G, int64_t r, float (&l)[3][4]) {
+#pragma unroll
+  for (int d = 0; d < 3; ++d) lagrange_f32<3>(G.s32[3 * r + d], l[d]);
+}
+template <>
+__device__ __forceinline__ void row_weights<float, 2>(const ApplyGeom& G, int64_t r, float (&l)[3][3]) {
+#pragma unroll
+  for (int d = 0; d < 3; ++d) lagrange_f32<2>(G.s32[3 * r + d], l[d]);
+}
+
+// Pass 1: w_r = (E x)_r for all rows.
+template <typename T, int P>
+__global__ void __launch_bounds__(256) k_erow_apply(ApplyGeom G, const T* __restrict__ x, T* __restrict__ w) {
+  const int rhs = blockIdx.y;
+  x += (int64_t)rhs * G.nA;
+  w += (int64_t)rhs * G.nR;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < G.nR; r += (int64_t)gridDim.x * blockDim.x) {
+    T l[3][P + 1];
+    row_weights<T, P>(G, r, l);
+    int b0 = G.rbase[3 * r], b1 = G.rbase[3 * r + 1], b2 = G.rbase[3 * r + 2];
+    T acc = 0;
+#pragma unroll
+    for (int u = 0; u <= P; ++u) {
+      T au = 0;
+#pragma unroll
+      for (int v = 0; v <= P; ++v) {
+        int32_t q = bm_rank_known(G.amap, G.g, b0 + u, b1 + v, b2);
+        const T* xp = x + q;
+        T av = 0;
+#pragma unroll
+        for (int t = 0; t <= P; ++t) av += l[2][t] * __ldg(xp + t);
+        au += l[1][v] * av;
+      }
+      acc += l[0][u] * au;
+    }
+    w[r] = acc;
+  }
+}
+
+// Pass 2: y_i = (c + 6/h^2) x_i - (1/h^2) sum_n w_n.
+template <typename T>
+__global__ void __launch_bounds__(256) k_stencil(ApplyGeom G, Shifts S, const T* __restrict__ x,
+                                                 const T* __restrict__ w, T* __restrict__ y) {
+  const int rhs = blockIdx.y;
+  x += (int64_t)rhs * G.nA;
+  y += (int64_t)rhs * G.nA;
+  w += (int64_t)rhs * G.nR;
+  const T diag = (T)(S.c[rhs] + 6.0 * G.coef), coef = (T)G.coef;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < G.nA; q += (int64_t)gridDim.x * blockDim.x) {
+    int i = G.ijkA[3 * q], j = G.ijkA[3 * q + 1], k = G.ijkA[3 * q + 2];
+    int32_t r = G.arow[q];
+    int32_t rjm = bm_rank_known(G.rmap, G.g, i, j - 1, k), rjp = bm_rank_known(G.rmap, G.g, i, j + 1, k);
+    int32_t rim = bm_rank_known(G.rmap, G.g, i - 1, j, k), rip = bm_rank_known(G.rmap, G.g, i + 1, j, k);
+    T s = ((w[rim] + w[rip]) + (w[rjm] + w[rjp])) + (w[r - 1] + w[r + 1]);
+    y[q] = diag * x[q] - coef * s;
+  }
+}
+
+// ---- transposed apply
+template <typename T>
+__global__ void k_loff_T(ApplyGeom G, const T* __restrict__ x, const int32_t* __restrict__ rijk, T* __restrict__ v) {
+  const int rhs = blockIdx.y;
+  x += (int64_t)rhs * G.nA;
+  v += (int64_t)rhs * G.nR;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < G.nR; r += (int64_t)gridDim.x * blockDim.x) {
+    int i = rijk[3 * r], j = rijk[3 * r + 1], k = rijk[3 * r + 2];
+    const int nb[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
+    T s = 0;
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+      int32_t m = bm_rank(G.amap, G.g, i + nb[d][0], j + nb[d][1], k + nb[d][2]);
+      if (m >= 0) s += x[m];
+    }
+    v[r] = s;
+  }
+}
+
+template <typename T, int P>
+__global__ void __launch_bounds__(256) k_ET(ApplyGeom G, Shifts S, const int64_t* __restrict__ tptr,
+                                            const uint32_t* __restrict__ tent, const T* __restrict__ x,
+                                            const T* __restrict__ v, T* __restrict__ y) {
+  const int rhs = blockIdx.y;
+  x += (int64_t)rhs * G.nA;
+  y += (int64_t)rhs * G.nA;
+  v += (int64_t)rhs * G.nR;
+  const T diag = (T)(S.c[rhs] + 6.0 * G.coef), coef = (T)G.coef;
+  constexpr int P1 = P + 1;
+  for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < G.nA; m += (int64_t)gridDim.x * blockDim.x) {
+    T acc = 0;
+    for (int64_t e = tptr[m]; e < tptr[m + 1]; ++e) {
+      uint32_t pk = tent[e];
+      int64_t r = pk >> 6;
+      int pos = pk & 63;
+      int u = pos / (P1 * P1), vv = (pos / P1) % P1, t = pos % P1;
+      T W;
+      if constexpr (sizeof(T) == 8) {
+        const double* w = G.w1d + r * 3 * P1;
+        W = (w[u] * w[P1 + vv]) * w[2 * P1 + t];
+      } else {
+        float l0[P1], l1[P1], l2[P1];
+        lagrange_f32<P>(G.s32[3 * r], l0);
+        lagrange_f32<P>(G.s32[3 * r + 1], l1);
+        lagrange_f32<P>(G.s32[3 * r + 2], l2);
+        W = (l0[u] * l1[vv]) * l2[t];
+      }
+      acc += W * v[r];
+    }
+    y[m] = diag * x[m] - coef * acc;
+  }
+}
+
+// transpose map: counts, then fill, then sort each segment
+__global__ void k_tcount(ApplyGeom G, int P, int32_t* cnt) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < G.nR; r += (int64_t)gridDim.x * blockDim.x) {
+    int b0 = G.rbase[3 * r], b1 = G.rbase[3 * r + 1], b2 = G.rbase[3 * r + 2];
+    for (int u = 0; u <= P; ++u)
+      for (int v = 0; v <= P; ++v) {
+        int32_t q = bm_rank_known(G.amap, G.g, b0 + u, b1 + v, b2);
+        for (int t = 0; t <= P; ++t) atomicAdd(&cnt[q + t], 1);
+      }
+  }
+}
+
+__global__ void k_tfill(ApplyGeom G, int P, const int64_t* __restrict__ tptr, int32_t* cursor, uint32_t* tent) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < G.nR; r += (int64_t)gridDim.x * blockDim.x) {
+    int b0 = G.rbase[3 * r], b1 = G.rbase[3 * r + 1], b2 = G.rbase[3 * r + 2];
+    int pos = 0;
+    for (int u = 0; u <= P; ++u)
+      for (int v = 0; v <= P; ++v) {
+        int32_t q = bm_rank_known(G.amap, G.g, b0 + u, b1 + v, b2);
+        for (int t = 0; t <= P; ++t, ++pos) {
+          int32_t slot = atomicAdd(&cursor[q + t], 1);
+          tent[tptr[q + t] + slot] = ((uint32_t)r << 6) | (uint32_t)pos;
+        }
+      }
+  }
+}
+
+__global__ void k_tsort(int64_t nA, const int64_t* __restrict__ tptr, uint32_t* tent) {
+  for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < nA; m += (int64_t)gridDim.x * blockDim.x) {
+    int64_t a = tptr[m], b = tptr[m + 1];
+    for (int64_t i = a + 1; i < b; ++i) {  // insertion sort (segments are short)
+      uint32_t key = tent[i];
+      int64_t j = i - 1;
+      while (j >= a && tent[j] > key) {
+        tent[j + 1] = tent[j];
+        --j;
+      }
+      tent[j + 1] = key;
+    }
+  }
+}
+
+ApplyGeom geom_of(const cpm_band* B) {
+  ApplyGeom G;
+  G.g = B->grid;
+  G.amap = B->amap;
+  G.rmap = B->rmap;
+  G.ijkA = B->ijkA;
+  G.arow = B->arow;
+  G.rbase = B->rbase;
+  G.w1d = B->w1d;
+  G.s32 = B->s32;
+  G.nA = B->nA;
+  G.nR = B->nR;
+  G.coef = 1.0 / (B->h * B->h);
+  return G;
+}
+
+template <typename T>
+cpm_status apply_typed(const cpm_band* B, const double* c, const T* x, T* y, int nrhs, int transpose, cudaStream_t s) {
+  ApplyGeom G = geom_of(B);
+  if (transpose && !B->tptr) CPM_TRY(build_transpose_map(const_cast<cpm_band*>(B), s));
+  for (int r0 = 0; r0 < nrhs; r0 += MAXRHS) {
+    int nr = nrhs - r0 < MAXRHS ? nrhs - r0 : MAXRHS;
+    Shifts S{};
+    for (int q = 0; q < nr; ++q) S.c[q] = c[r0 + q];
+    T* w = nullptr;
+    CPM_TRY(dalloc(&w, (size_t)nr * B->nR, s));
+    const T* xr = x + (int64_t)r0 * B->nA;
+    T* yr = y + (int64_t)r0 * B->nA;
+    if (!transpose) {
+      dim3 g1(grid_for(B->nR, 256), nr), g2(grid_for(B->nA, 256), nr);
+      if (B->p == 3) k_erow_apply<T, 3><<<g1, 256, 0, s>>>(G, xr, w);
+      else k_erow_apply<T, 2><<<g1, 256, 0, s>>>(G, xr, w);
+      k_stencil<T><<<g2, 256, 0, s>>>(G, S, xr, w, yr);
+    } else {
+      dim3 g1(grid_for(B->nR, 256), nr), g2(grid_for(B->nA, 256), nr);
+      k_loff_T<T><<<g1, 256, 0, s>>>(G, xr, B->rijk, w);
+      if (B->p == 3) k_ET<T, 3><<<g2, 256, 0, s>>>(G, S, B->tptr, B->tent, xr, w, yr);
+      else k_ET<T, 2><<<g2, 256, 0, s>>>(G, S, B->tptr, B->tent, xr, w, yr);
+    }
+    cudaError_t e = cudaGetLastError();
+    dfree(w, s);
+    if (e != cudaSuccess) return cuda_fail(e, "apply kernels", __FILE__, __LINE__);
+  }
+  return CPM_OK;
+}
+
+}  // namespace
+
+cpm_status build_transpose_map(cpm_band* B, cudaStream_t s) {
+  ApplyGeom G = geom_of(B);
+  int P = B->p;
+  int64_t nA = B->nA;
+  int32_t* cnt = nullptr;
+  CPM_TRY(dalloc(&cnt, nA, s));
+  CPM_TRY(dalloc(&B->tptr, nA + 1, s));
+  CPM_CUDA(cudaMemsetAsync(cnt, 0, nA * sizeof(int32_t), s));
+  k_tcount<<<grid_for(B->nR, 256), 256, 0, s>>>(G, P, cnt);
+  CPM_TRY(scan_exclusive_i32(cnt, B->tptr, nA, s));
+  int64_t total = 0;
+  CPM_CUDA(cudaMemcpyAsync(&total, B->tptr + nA, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  CPM_CUDA(cudaStreamSynchronize(s));
+  CPM_TRY(dalloc(&B->tent, total, s));
+  CPM_CUDA(cudaMemsetAsync(cnt, 0, nA * sizeof(int32_t), s));
+  k_tfill<<<grid_for(B->nR, 256), 256, 0, s>>>(G, P, B->tptr, cnt, B->tent);
+  k_tsort<<<grid_for(nA, 128), 128, 0, s>>>(nA, B->tptr, B->tent);
+  CPM_CUDA(cudaGetLastError());
+  dfree(cnt, s);
+  return CPM_OK;
+}
+
+cpm_status apply_op(const cpm_band* B, const double* c, const void* x, void* y, cpm_dtype dt, int nrhs, int transpose,
+                    cudaStream_t s) {
+  if (dt == CPM_F64) return apply_typed<double>(B, c, (const double*)x, (double*)y, nrhs, transpose, s);
+  if (dt == CPM_F32) return apply_typed<float>(B, c, (const float*)x, (float*)y, nrhs, transpose, s);
+  return fail(CPM_ERR_ARG, "cpm_apply supports CPM_F64 and CPM_F32 vectors");
+}
+
+}  // namespace cpm

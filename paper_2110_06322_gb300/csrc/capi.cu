@@ -1,0 +1,156 @@
+// capi.cu -- extern "C" entry points of libcpm (declared in include/cpm.h).
+// Argument checking and error reporting live here; the work is in band.cu,
+// apply.cu, oras.cu and solve.cu.
+#include <cmath>
+#include <cstring>
+
+#include "kernels.cuh"
+#include "oras.cuh"
+
+namespace cpm {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+cpm_status fail(cpm_status st, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+cpm_status cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
+  snprintf(g_err, sizeof(g_err), "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+  return e == cudaErrorMemoryAllocation ? CPM_ERR_OOM : CPM_ERR_CUDA;
+}
+
+}  // namespace cpm
+
+using namespace cpm;
+
+static cudaStream_t as_stream(void* s) { return (cudaStream_t)s; }
+
+extern "C" {
+
+const char* cpm_last_error(void) { return g_err; }
+
+cpm_status cpm_band_build(const cpm_surface* surf, double h, int p, void* stream, cpm_band** out) {
+  g_err[0] = 0;
+  return band_build(surf, h, p, as_stream(stream), out);
+}
+
+cpm_status cpm_band_info(const cpm_band* band, int64_t* n_active, int64_t* n_ghost, int64_t* n_tube) {
+  if (!band) return fail(CPM_ERR_ARG, "null band");
+  if (n_active) *n_active = band->nA;
+  if (n_ghost) *n_ghost = band->nG;
+  if (n_tube) *n_tube = band->nT;
+  return CPM_OK;
+}
+
+cpm_status cpm_band_export(const cpm_band* band, int32_t* ijk_active, int32_t* ijk_ghost, int32_t* erow_base,
+                           double* erow_cp, int64_t* perm, void* stream) {
+  if (!band) return fail(CPM_ERR_ARG, "null band");
+  return band_export(band, ijk_active, ijk_ghost, erow_base, erow_cp, perm, as_stream(stream));
+}
+
+cpm_status cpm_band_weights(const cpm_band* band, double* w1d, void* stream) {
+  if (!band || !w1d) return fail(CPM_ERR_ARG, "null argument");
+  return band_weights(band, w1d, as_stream(stream));
+}
+
+cpm_status cpm_apply(const cpm_band* band, const double* c, const void* x, void* y, cpm_dtype dtype, int nrhs,
+                     int transpose, void* stream) {
+  if (!band || !c || !x || !y) return fail(CPM_ERR_ARG, "null argument");
+  if (nrhs < 1) return fail(CPM_ERR_ARG, "nrhs must be >= 1");
+  if (x == y) return fail(CPM_ERR_ARG, "x and y must not overlap");
+  for (int q = 0; q < nrhs; ++q)
+    if (!std::isfinite(c[q])) return fail(CPM_ERR_NAN, "shift c[%d] is not finite", q);
+  return apply_op(band, c, x, y, dtype, nrhs, transpose ? 1 : 0, as_stream(stream));
+}
+
+cpm_status oras_setup(const cpm_band* band, const oras_params* prm, double c, void* stream, oras_pc** out) {
+  if (!band || !prm || !out) return fail(CPM_ERR_ARG, "null argument");
+  *out = nullptr;
+  if (prm->nparts < 1 || prm->nparts > band->nA) return fail(CPM_ERR_ARG, "nparts must be in [1, N_A]");
+  if (prm->overlap < 0 || prm->overlap > 16) return fail(CPM_ERR_ARG, "overlap must be in [0, 16]");
+  if (prm->robin && !(prm->alpha >= 0.0 && prm->alpha_cross >= 0.0))
+    return fail(CPM_ERR_ARG, "Robin parameters must be >= 0 (infinity allowed)");
+  if (prm->store != CPM_F32 && prm->store != CPM_BF16 && prm->store != CPM_F64)
+    return fail(CPM_ERR_ARG, "store must be CPM_F64, CPM_F32 or CPM_BF16");
+  if (!std::isfinite(c)) return fail(CPM_ERR_NAN, "shift c is not finite");
+  g_err[0] = 0;
+  return oras_build(band, prm, c, as_stream(stream), out);
+}
+
+cpm_status oras_apply(const oras_pc* pc, const void* r, void* z, cpm_dtype dtype, int nrhs, int transpose,
+                      void* stream) {
+  if (!pc || !r || !z) return fail(CPM_ERR_ARG, "null argument");
+  if (r == z) return fail(CPM_ERR_ARG, "r and z must not overlap");
+  if (nrhs < 1) return fail(CPM_ERR_ARG, "nrhs must be >= 1");
+  if (dtype != CPM_F64 && dtype != CPM_F32) return fail(CPM_ERR_ARG, "oras_apply supports CPM_F64 and CPM_F32");
+  return oras_run(pc, r, z, dtype, nrhs, transpose ? 1 : 0, as_stream(stream));
+}
+
+cpm_status oras_info(const oras_pc* pc, int32_t* nparts, int64_t* total_rows, int64_t* total_nnz,
+                     int32_t* max_levels) {
+  if (!pc) return fail(CPM_ERR_ARG, "null preconditioner");
+  if (nparts) *nparts = pc->np;
+  if (total_rows) *total_rows = pc->nloc;
+  if (total_nnz) *total_nnz = pc->nnz;
+  if (max_levels) *max_levels = pc->max_levels;
+  return CPM_OK;
+}
+
+cpm_status oras_export(const oras_pc* pc, int32_t* part, int64_t* sub_ptr, int32_t* sub_nodes, void* stream) {
+  if (!pc) return fail(CPM_ERR_ARG, "null preconditioner");
+  cudaStream_t s = as_stream(stream);
+  if (part) CPM_CUDA(cudaMemcpyAsync(part, pc->part, pc->nA * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+  if (sub_ptr) CPM_CUDA(cudaMemcpyAsync(sub_ptr, pc->sptr, (pc->np + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+  if (sub_nodes) CPM_CUDA(cudaMemcpyAsync(sub_nodes, pc->snode, pc->nloc * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+  return CPM_OK;
+}
+
+cpm_status cpm_solve(const cpm_band* band, const oras_pc* pc, double c, const double* f, double* u,
+                     const cpm_solve_params* prm, cpm_solve_info* info, void* stream) {
+  if (!band || !f || !u || !prm || !info) return fail(CPM_ERR_ARG, "null argument");
+  if (prm->restart < 1 || prm->restart > 256 || prm->maxit < 0 || !(prm->rtol > 0.0))
+    return fail(CPM_ERR_ARG, "restart in [1, 256], maxit >= 0 and rtol > 0 required");
+  if (!std::isfinite(c)) return fail(CPM_ERR_NAN, "shift c is not finite");
+  if (pc && pc->band != band) return fail(CPM_ERR_ARG, "preconditioner was built for another band");
+  g_err[0] = 0;
+  return solve_run(band, pc, c, f, u, prm, info, 0, as_stream(stream));
+}
+
+cpm_status cpm_solve_adjoint(const cpm_band* band, const oras_pc* pc, double c, const double* g, double* lambda,
+                             const cpm_solve_params* prm, cpm_solve_info* info, void* stream) {
+  if (!band || !g || !lambda || !prm || !info) return fail(CPM_ERR_ARG, "null argument");
+  if (prm->restart < 1 || prm->restart > 256 || prm->maxit < 0 || !(prm->rtol > 0.0))
+    return fail(CPM_ERR_ARG, "restart in [1, 256], maxit >= 0 and rtol > 0 required");
+  if (!std::isfinite(c)) return fail(CPM_ERR_NAN, "shift c is not finite");
+  if (pc && pc->band != band) return fail(CPM_ERR_ARG, "preconditioner was built for another band");
+  g_err[0] = 0;
+  return solve_run(band, pc, c, g, lambda, prm, info, 1, as_stream(stream));
+}
+
+void cpm_band_free(cpm_band* band) {
+  if (!band) return;
+  cudaDeviceSynchronize();
+  band_free(band, 0);
+  cudaDeviceSynchronize();
+}
+
+void oras_free(oras_pc* pc) {
+  if (!pc) return;
+  cudaDeviceSynchronize();
+  oras_destroy(pc, 0);
+  cudaDeviceSynchronize();
+}
+
+}  // extern "C"

@@ -1,0 +1,125 @@
+// common.cuh -- internal definitions shared by the libcpm translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <vector>
+
+#include "cpm.h"
+
+namespace cpm {
+
+// ------------------------------------------------------------------ errors
+void set_error(const char* fmt, ...);
+cpm_status fail(cpm_status st, const char* fmt, ...);
+cpm_status cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define CPM_CUDA(call)                                                     \
+  do {                                                                     \
+    cudaError_t e_ = (call);                                               \
+    if (e_ != cudaSuccess) return ::cpm::cuda_fail(e_, #call, __FILE__, __LINE__); \
+  } while (0)
+
+#define CPM_TRY(expr)                    \
+  do {                                   \
+    cpm_status s_ = (expr);              \
+    if (s_ != CPM_OK) return s_;         \
+  } while (0)
+
+// Device allocation that reports CPM_ERR_OOM.  Stream-ordered.
+template <typename T>
+cpm_status dalloc(T** p, size_t n, cudaStream_t s) {
+  *p = nullptr;
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMallocAsync((void**)p, n * sizeof(T), s);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return fail(CPM_ERR_OOM, "device allocation of %zu bytes failed", n * sizeof(T));
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync", __FILE__, __LINE__);
+  return CPM_OK;
+}
+
+template <typename T>
+void dfree(T*& p, cudaStream_t s) {
+  if (p) cudaFreeAsync((void*)p, s);
+  p = nullptr;
+}
+
+inline int grid_for(int64_t n, int block, int64_t cap = 152 * 64) {
+  int64_t g = (n + block - 1) / block;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+// ------------------------------------------------------------------ lattice bitmaps
+// A set of lattice cells stored as one bit per cell over a dense box grid
+// (origin glo, extents gn), k fastest.  Each k-column is padded to whole
+// 64-bit words; `pre` holds the number of set bits before the word, so the
+// canonical rank of a member cell is pre + popcount of the bits below it.
+struct __align__(16) BitWord {
+  unsigned long long bits;
+  int32_t pre;
+  int32_t pad;
+};
+
+struct Grid {
+  int glo[3];
+  int gn[3];
+  int nkw;  // 64-bit words per k-column
+  __host__ __device__ int64_t nwords() const { return (int64_t)gn[0] * gn[1] * nkw; }
+};
+
+// rank of lattice cell (i,j,k) in a bitmap, or -1 when absent / outside
+__device__ __forceinline__ int32_t bm_rank(const BitWord* __restrict__ bm, const Grid& g, int i, int j, int k) {
+  int a = i - g.glo[0], b = j - g.glo[1], c = k - g.glo[2];
+  if ((unsigned)a >= (unsigned)g.gn[0] || (unsigned)b >= (unsigned)g.gn[1] || (unsigned)c >= (unsigned)(g.nkw * 64))
+    return -1;
+  int64_t w = ((int64_t)a * g.gn[1] + b) * g.nkw + (c >> 6);
+  BitWord bw = bm[w];
+  unsigned long long bit = 1ull << (c & 63);
+  if (!(bw.bits & bit)) return -1;
+  return bw.pre + __popcll(bw.bits & (bit - 1));
+}
+
+// rank of a cell known to be present (no membership test)
+__device__ __forceinline__ int32_t bm_rank_known(const BitWord* __restrict__ bm, const Grid& g, int i, int j, int k) {
+  int a = i - g.glo[0], b = j - g.glo[1], c = k - g.glo[2];
+  int64_t w = ((int64_t)a * g.gn[1] + b) * g.nkw + (c >> 6);
+  BitWord bw = bm[w];
+  return bw.pre + __popcll(bw.bits & ((1ull << (c & 63)) - 1));
+}
+
+}  // namespace cpm
+
+// ------------------------------------------------------------------ handles
+struct cpm_band {
+  int device = 0;
+  cpm_surface surf{};
+  double h = 0, lam = 0;
+  int p = 3;
+  cpm::Grid grid{};
+  int64_t nT = 0, nA = 0, nG = 0, nR = 0;
+  cpm::BitWord* amap = nullptr;  // Sigma_A
+  cpm::BitWord* rmap = nullptr;  // Sigma_A u Sigma_G ("rows")
+  int32_t* ijkA = nullptr;       // [nA][3] canonical
+  int32_t* arow = nullptr;       // [nA] row (rank in rmap) of each active node
+  int32_t* rijk = nullptr;       // [nR][3] row nodes, canonical in rmap order
+  int32_t* rexp = nullptr;       // [nR] export position (active rows, then ghost rows)
+  int32_t* rbase = nullptr;      // [nR][3] interpolation cube base
+  double* rcp = nullptr;         // [nR][3] closest point (FP64)
+  double* w1d = nullptr;         // [nR][3][p+1] barycentric 1-D weights (FP64)
+  float* s32 = nullptr;          // [nR][3] cube offsets s = cp/h - base (FP32)
+  // transpose map (built on first transposed apply): for each active m, the
+  // (row, cube position) pairs whose cube holds m, ascending row
+  int64_t* tptr = nullptr;       // [nA + 1]
+  uint32_t* tent = nullptr;      // packed row * 64 + position
+  // scratch for the operator apply
+  void* wbuf = nullptr;          // [nR] E x values (FP64 room)
+  size_t wbuf_bytes = 0;
+};

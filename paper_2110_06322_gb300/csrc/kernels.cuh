@@ -1,0 +1,27 @@
+// kernels.cuh -- cross-translation-unit entry points of libcpm (internal).
+#pragma once
+
+#include "common.cuh"
+
+namespace cpm {
+
+// scan.cu: exclusive prefix sums, out[0..n] (out[n] = total), deterministic
+cpm_status scan_exclusive_i32(const int32_t* in, int64_t* out, int64_t n, cudaStream_t s);
+cpm_status scan_exclusive_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s);
+
+// band.cu
+cpm_status band_build(const cpm_surface* surf, double h, int p, cudaStream_t s, cpm_band** out);
+void band_free(cpm_band* B, cudaStream_t s);
+cpm_status band_export(const cpm_band* B, int32_t* ijkA, int32_t* ijkG, int32_t* ebase, double* ecp, int64_t* perm,
+                       cudaStream_t s);
+cpm_status band_weights(const cpm_band* B, double* w, cudaStream_t s);
+cpm_status bitmap_prefix(BitWord* bm, int64_t nw, int64_t* total, cudaStream_t s);
+
+// apply.cu: y = M x or M^T x for nrhs vectors of type T (double or float)
+cpm_status apply_op(const cpm_band* B, const double* c, const void* x, void* y, cpm_dtype dt, int nrhs, int transpose,
+                    cudaStream_t s);
+// E x for all rows (into B->wbuf) followed by the stencil; exposed so that
+// the solver can reuse it with device-side c.
+cpm_status build_transpose_map(cpm_band* B, cudaStream_t s);
+
+}  // namespace cpm

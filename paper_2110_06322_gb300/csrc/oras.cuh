@@ -1,0 +1,54 @@
+// oras.cuh -- Schwarz preconditioner handle and solver entry points (internal).
+#pragma once
+
+#include "common.cuh"
+
+// Restricted additive Schwarz preconditioner (Section 2.2).  Local rows of all
+// subdomains are numbered globally ("local rows"): subdomain j owns local
+// rows sptr[j] .. sptr[j+1]-1, in its local order.  Column indices in the
+// factors are local to the subdomain (0 .. |S_j|-1).
+struct oras_pc {
+  const cpm_band* band = nullptr;
+  int device = 0;
+  int np = 0, overlap = 0, robin = 0, store = CPM_F32;
+  double alpha = 0, alpha_x = 0, c = 0;
+  int64_t nA = 0;
+  int32_t* part = nullptr;    // [nA] disjoint part of each active node
+  int64_t nloc = 0;           // sum_j |S_j|
+  int64_t* sptr = nullptr;    // [np+1]
+  int32_t* snode = nullptr;   // [nloc] canonical node of each local row
+  uint8_t* owned = nullptr;   // [nloc] node lies in the subdomain's own disjoint part
+  int64_t nnz = 0;
+  int64_t* rptr = nullptr;    // [nloc+1] CSR of the local matrices / ILU(0) factors (L\U packed)
+  int32_t* col = nullptr;     // [nnz] local column (within the subdomain)
+  int32_t* dpos = nullptr;    // [nloc] offset of the diagonal within its row
+  double* val = nullptr;      // [nnz] FP64 factors
+  float* val32 = nullptr;     // [nnz] FP32 factors (store == CPM_F32)
+  __nv_bfloat16* val16 = nullptr;  // [nnz] BF16 factors (store == CPM_BF16)
+  // level schedules: for subdomain j, forward levels lvptr_f[lvsub_f[j] .. lvsub_f[j+1]]
+  // index ranges of lvrow_f (local rows, ascending within a level)
+  int32_t* lvsub_f = nullptr;  // [np+1]
+  int64_t* lvptr_f = nullptr;  // [nlev_f + 1]
+  int32_t* lvrow_f = nullptr;  // [nloc]
+  int32_t* lvsub_b = nullptr;
+  int64_t* lvptr_b = nullptr;
+  int32_t* lvrow_b = nullptr;
+  int32_t max_levels = 0;
+  // transposed factors (adjoint): CSR of L^T and U^T, built on first use
+  int64_t* tptr = nullptr;
+  int32_t* tcol = nullptr;
+  double* tval = nullptr;
+  float* tval32 = nullptr;
+  int32_t* tdpos = nullptr;
+  // node -> (subdomain, local row) memberships, for the adjoint's gather
+  int64_t* mptr = nullptr;    // [nA+1]
+  int64_t* mrow = nullptr;    // local rows, ascending subdomain
+};
+
+namespace cpm {
+cpm_status oras_build(const cpm_band* B, const oras_params* prm, double c, cudaStream_t s, oras_pc** out);
+cpm_status oras_run(const oras_pc* P, const void* r, void* z, cpm_dtype dt, int nrhs, int transpose, cudaStream_t s);
+void oras_destroy(oras_pc* P, cudaStream_t s);
+cpm_status solve_run(const cpm_band* B, const oras_pc* P, double c, const double* f, double* u,
+                     const cpm_solve_params* prm, cpm_solve_info* info, int transpose, cudaStream_t s);
+}  // namespace cpm
