@@ -166,6 +166,8 @@ typedef struct {
   int32_t mixed;
   int32_t reorth;
   double inner_rtol;  /* mixed only: relative tolerance of each inner solve */
+  int32_t timing;     /* 1: time the preconditioner and operator applies with CUDA
+                         events on `stream` (adds one event wait per apply) */
 } cpm_solve_params;
 
 typedef struct {
@@ -174,6 +176,10 @@ typedef struct {
   int32_t ir_steps;      /* refinement steps (mixed) */
   double rel_residual;   /* |f - M u|_2 / |f|_2 in FP64 at exit */
   int32_t status;        /* cpm_status of the solve */
+  double ms_precond;     /* timing = 1: total milliseconds in preconditioner applies */
+  double ms_operator;    /* timing = 1: total milliseconds in operator applies */
+  int32_t n_precond;     /* number of preconditioner applies */
+  int32_t n_operator;    /* number of operator applies */
 } cpm_solve_info;
 
 /* cpm_solve -- solve M u = f.  f: DEVICE, N_A doubles.  u: DEVICE, N_A
@@ -189,6 +195,11 @@ cpm_status cpm_solve_adjoint(const cpm_band* band, const oras_pc* pc, double c, 
 
 void cpm_band_free(cpm_band* band);
 void oras_free(oras_pc* pc);
+
+/* Total number of CUDA kernels this library has launched since it was loaded
+ * (all threads).  The difference of two readings counts the kernels of the
+ * calls made in between. */
+int64_t cpm_kernel_launches(void);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* cpm_last_error(void);

@@ -38,12 +38,13 @@ class oras_params(C.Structure):
 
 class cpm_solve_params(C.Structure):
     _fields_ = [("restart", C.c_int32), ("maxit", C.c_int32), ("rtol", C.c_double), ("mixed", C.c_int32),
-                ("reorth", C.c_int32), ("inner_rtol", C.c_double)]
+                ("reorth", C.c_int32), ("inner_rtol", C.c_double), ("timing", C.c_int32)]
 
 
 class cpm_solve_info(C.Structure):
     _fields_ = [("iters", C.c_int32), ("restarts", C.c_int32), ("ir_steps", C.c_int32),
-                ("rel_residual", C.c_double), ("status", C.c_int32)]
+                ("rel_residual", C.c_double), ("status", C.c_int32), ("ms_precond", C.c_double),
+                ("ms_operator", C.c_double), ("n_precond", C.c_int32), ("n_operator", C.c_int32)]
 
 
 class CpmError(RuntimeError):
@@ -77,6 +78,7 @@ def lib():
         "cpm_solve_adjoint": (i32, [vp, vp, f64, vp, vp, P(cpm_solve_params), P(cpm_solve_info), vp]),
         "cpm_band_free": (None, [vp]),
         "oras_free": (None, [vp]),
+        "cpm_kernel_launches": (C.c_int64, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -88,7 +90,7 @@ def lib():
 
 EXPORTED = ["cpm_last_error", "cpm_band_build", "cpm_band_info", "cpm_band_export", "cpm_band_weights", "cpm_apply",
             "oras_setup", "oras_apply", "oras_info", "oras_export", "cpm_solve", "cpm_solve_adjoint", "cpm_band_free",
-            "oras_free"]
+            "oras_free", "cpm_kernel_launches"]
 
 
 def _check(st):
@@ -146,16 +148,21 @@ def oras_apply(pc, r, z, n_active, transpose=False, stream=None):
 
 
 def cpm_solve(band, pc, c, f, u, restart=30, maxit=10000, rtol=1e-8, mixed=False, reorth=True, inner_rtol=1e-4,
-              adjoint=False, stream=None):
+              adjoint=False, timing=False, stream=None):
     prm = cpm_solve_params(int(restart), int(maxit), float(rtol), int(bool(mixed)), int(bool(reorth)),
-                           float(inner_rtol))
+                           float(inner_rtol), int(bool(timing)))
     info = cpm_solve_info()
     fn = lib().cpm_solve_adjoint if adjoint else lib().cpm_solve
     st = fn(band, pc, float(c), _ptr(f), _ptr(u), C.byref(prm), C.byref(info), _stream(stream))
     if st not in (CPM_OK, CPM_ERR_NOT_CONVERGED):
         _check(st)
     return {"status": st, "iters": info.iters, "restarts": info.restarts, "ir_steps": info.ir_steps,
-            "rel_residual": info.rel_residual}
+            "rel_residual": info.rel_residual, "ms_precond": info.ms_precond, "ms_operator": info.ms_operator,
+            "n_precond": info.n_precond, "n_operator": info.n_operator}
+
+
+def cpm_kernel_launches():
+    return lib().cpm_kernel_launches()
 
 
 def cpm_solve_adjoint(band, pc, c, g, lam, **kw):

@@ -9,6 +9,13 @@
 // Pass 2 (k_stencil) forms the 7-point stencil from those values; the +-k
 // neighbours of a row are the adjacent rows.
 //
+// FP32 uses a difference form: the weights of an E row sum to one, so
+//   (E x)_n - x_i = sum_m W_nm (x_m - x_ref(n)) + (x_ref(n) - x_i)
+// with x_ref(n) a node of row n's own cube.  Rounding then scales with the
+// local differences of x instead of |x| * 6/h^2, which keeps the FP32
+// operator accurate for smooth vectors on fine grids (at h = 0.004 the direct
+// form loses about 4e-3 of relative accuracy to cancellation).
+//
 // The transposed apply uses y = (c + 6/h^2) x - (1/h^2) E^T (L_off^T x):
 // v_r = sum of x over the active neighbours of row r, then E^T v gathered
 // through a transpose map (for each active m, its (row, position) pairs in
@@ -79,16 +86,20 @@ __device__ __forceinline__ void row_weights<float, 2>(const ApplyGeom& G, int64_
   for (int d = 0; d < 3; ++d) lagrange_f32<2>(G.s32[3 * r + d], l[d]);
 }
 
-// Pass 1: w_r = (E x)_r for all rows.
+// Pass 1: w_r = (E x)_r for all rows (FP64), or the difference-form pair
+// (sum_m W_rm (x_m - x_ref), x_ref) (FP32).
 template <typename T, int P>
 __global__ void __launch_bounds__(256) k_erow_apply(ApplyGeom G, const T* __restrict__ x, T* __restrict__ w) {
+  constexpr bool DIFF = sizeof(T) == 4;
   const int rhs = blockIdx.y;
   x += (int64_t)rhs * G.nA;
-  w += (int64_t)rhs * G.nR;
+  w += (int64_t)rhs * G.nR * (DIFF ? 2 : 1);
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < G.nR; r += (int64_t)gridDim.x * blockDim.x) {
     T l[3][P + 1];
     row_weights<T, P>(G, r, l);
     int b0 = G.rbase[3 * r], b1 = G.rbase[3 * r + 1], b2 = G.rbase[3 * r + 2];
+    T xref = 0;
+    if (DIFF) xref = __ldg(x + bm_rank_known(G.amap, G.g, b0 + 1, b1 + 1, b2) + 1);
     T acc = 0;
 #pragma unroll
     for (int u = 0; u <= P; ++u) {
@@ -99,12 +110,17 @@ __global__ void __launch_bounds__(256) k_erow_apply(ApplyGeom G, const T* __rest
         const T* xp = x + q;
         T av = 0;
 #pragma unroll
-        for (int t = 0; t <= P; ++t) av += l[2][t] * __ldg(xp + t);
+        for (int t = 0; t <= P; ++t) av += l[2][t] * (__ldg(xp + t) - xref);
         au += l[1][v] * av;
       }
       acc += l[0][u] * au;
     }
-    w[r] = acc;
+    if (DIFF) {
+      w[2 * r] = acc;
+      w[2 * r + 1] = xref;
+    } else {
+      w[r] = acc;
+    }
   }
 }
 
@@ -115,15 +131,23 @@ __global__ void __launch_bounds__(256) k_stencil(ApplyGeom G, Shifts S, const T*
   const int rhs = blockIdx.y;
   x += (int64_t)rhs * G.nA;
   y += (int64_t)rhs * G.nA;
-  w += (int64_t)rhs * G.nR;
-  const T diag = (T)(S.c[rhs] + 6.0 * G.coef), coef = (T)G.coef;
+  constexpr bool DIFF = sizeof(T) == 4;
+  w += (int64_t)rhs * G.nR * (DIFF ? 2 : 1);
+  const T diag = (T)(S.c[rhs] + 6.0 * G.coef), coef = (T)G.coef, cshift = (T)S.c[rhs];
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < G.nA; q += (int64_t)gridDim.x * blockDim.x) {
     int i = G.ijkA[3 * q], j = G.ijkA[3 * q + 1], k = G.ijkA[3 * q + 2];
     int32_t r = G.arow[q];
     int32_t rjm = bm_rank_known(G.rmap, G.g, i, j - 1, k), rjp = bm_rank_known(G.rmap, G.g, i, j + 1, k);
     int32_t rim = bm_rank_known(G.rmap, G.g, i - 1, j, k), rip = bm_rank_known(G.rmap, G.g, i + 1, j, k);
-    T s = ((w[rim] + w[rip]) + (w[rjm] + w[rjp])) + (w[r - 1] + w[r + 1]);
-    y[q] = diag * x[q] - coef * s;
+    const T xi = x[q];
+    if (DIFF) {
+      auto d = [&](int32_t n) { return w[2 * n] + (w[2 * n + 1] - xi); };
+      T s = ((d(rim) + d(rip)) + (d(rjm) + d(rjp))) + (d(r - 1) + d(r + 1));
+      y[q] = cshift * xi - coef * s;
+    } else {
+      T s = ((w[rim] + w[rip]) + (w[rjm] + w[rjp])) + (w[r - 1] + w[r + 1]);
+      y[q] = diag * xi - coef * s;
+    }
   }
 }
 
@@ -247,19 +271,19 @@ cpm_status apply_typed(const cpm_band* B, const double* c, const T* x, T* y, int
     Shifts S{};
     for (int q = 0; q < nr; ++q) S.c[q] = c[r0 + q];
     T* w = nullptr;
-    CPM_TRY(dalloc(&w, (size_t)nr * B->nR, s));
+    CPM_TRY(dalloc(&w, (size_t)nr * B->nR * (sizeof(T) == 4 ? 2 : 1), s));
     const T* xr = x + (int64_t)r0 * B->nA;
     T* yr = y + (int64_t)r0 * B->nA;
     if (!transpose) {
       dim3 g1(grid_for(B->nR, 256), nr), g2(grid_for(B->nA, 256), nr);
-      if (B->p == 3) k_erow_apply<T, 3><<<g1, 256, 0, s>>>(G, xr, w);
-      else k_erow_apply<T, 2><<<g1, 256, 0, s>>>(G, xr, w);
-      k_stencil<T><<<g2, 256, 0, s>>>(G, S, xr, w, yr);
+      if (B->p == 3) KL(k_erow_apply<T, 3><<<g1, 256, 0, s>>>(G, xr, w));
+      else KL(k_erow_apply<T, 2><<<g1, 256, 0, s>>>(G, xr, w));
+      KL(k_stencil<T><<<g2, 256, 0, s>>>(G, S, xr, w, yr));
     } else {
       dim3 g1(grid_for(B->nR, 256), nr), g2(grid_for(B->nA, 256), nr);
-      k_loff_T<T><<<g1, 256, 0, s>>>(G, xr, B->rijk, w);
-      if (B->p == 3) k_ET<T, 3><<<g2, 256, 0, s>>>(G, S, B->tptr, B->tent, xr, w, yr);
-      else k_ET<T, 2><<<g2, 256, 0, s>>>(G, S, B->tptr, B->tent, xr, w, yr);
+      KL(k_loff_T<T><<<g1, 256, 0, s>>>(G, xr, B->rijk, w));
+      if (B->p == 3) KL(k_ET<T, 3><<<g2, 256, 0, s>>>(G, S, B->tptr, B->tent, xr, w, yr));
+      else KL(k_ET<T, 2><<<g2, 256, 0, s>>>(G, S, B->tptr, B->tent, xr, w, yr));
     }
     cudaError_t e = cudaGetLastError();
     dfree(w, s);
@@ -278,15 +302,15 @@ cpm_status build_transpose_map(cpm_band* B, cudaStream_t s) {
   CPM_TRY(dalloc(&cnt, nA, s));
   CPM_TRY(dalloc(&B->tptr, nA + 1, s));
   CPM_CUDA(cudaMemsetAsync(cnt, 0, nA * sizeof(int32_t), s));
-  k_tcount<<<grid_for(B->nR, 256), 256, 0, s>>>(G, P, cnt);
+  KL(k_tcount<<<grid_for(B->nR, 256), 256, 0, s>>>(G, P, cnt));
   CPM_TRY(scan_exclusive_i32(cnt, B->tptr, nA, s));
   int64_t total = 0;
   CPM_CUDA(cudaMemcpyAsync(&total, B->tptr + nA, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   CPM_CUDA(cudaStreamSynchronize(s));
   CPM_TRY(dalloc(&B->tent, total, s));
   CPM_CUDA(cudaMemsetAsync(cnt, 0, nA * sizeof(int32_t), s));
-  k_tfill<<<grid_for(B->nR, 256), 256, 0, s>>>(G, P, B->tptr, cnt, B->tent);
-  k_tsort<<<grid_for(nA, 128), 128, 0, s>>>(nA, B->tptr, B->tent);
+  KL(k_tfill<<<grid_for(B->nR, 256), 256, 0, s>>>(G, P, B->tptr, cnt, B->tent));
+  KL(k_tsort<<<grid_for(nA, 128), 128, 0, s>>>(nA, B->tptr, B->tent));
   CPM_CUDA(cudaGetLastError());
   dfree(cnt, s);
   return CPM_OK;

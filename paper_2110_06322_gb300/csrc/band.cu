@@ -19,92 +19,11 @@
 
 #include "common.cuh"
 #include "kernels.cuh"
+#include "surface.cuh"
 
 namespace cpm {
 
 namespace {
-
-__device__ __forceinline__ double dm(double a, double b) { return __dmul_rn(a, b); }
-__device__ __forceinline__ double da(double a, double b) { return __dadd_rn(a, b); }
-__device__ __forceinline__ double dsb(double a, double b) { return __dsub_rn(a, b); }
-__device__ __forceinline__ double ddv(double a, double b) { return __ddiv_rn(a, b); }
-
-struct SurfDev {
-  int kind;
-  double c[3];
-  double a, b;
-};
-
-// unsigned distance to the surface (defined everywhere)
-__device__ double surf_dist(const SurfDev& S, double x0, double x1, double x2) {
-  double dx = dsb(x0, S.c[0]), dy = dsb(x1, S.c[1]), dz = dsb(x2, S.c[2]);
-  if (S.kind == 0) {
-    double n = __dsqrt_rn(da(da(dm(dx, dx), dm(dy, dy)), dm(dz, dz)));
-    return fabs(dsb(n, S.a));
-  }
-  double rxy = __dsqrt_rn(da(dm(dx, dx), dm(dy, dy)));
-  double w = dsb(rxy, S.a);
-  double n = __dsqrt_rn(da(dm(w, w), dm(dz, dz)));
-  return fabs(dsb(n, S.b));
-}
-
-// closest point (eq. cpFunc): sphere -- radial projection; torus -- nearest
-// point of the core circle, then r along the direction to x
-__device__ bool surf_cp(const SurfDev& S, double x0, double x1, double x2, double cp[3]) {
-  double dx = dsb(x0, S.c[0]), dy = dsb(x1, S.c[1]), dz = dsb(x2, S.c[2]);
-  if (S.kind == 0) {
-    double n = __dsqrt_rn(da(da(dm(dx, dx), dm(dy, dy)), dm(dz, dz)));
-    if (!(n > 0.0)) return false;
-    double q = ddv(S.a, n);
-    cp[0] = da(S.c[0], dm(q, dx));
-    cp[1] = da(S.c[1], dm(q, dy));
-    cp[2] = da(S.c[2], dm(q, dz));
-    return true;
-  }
-  double rxy = __dsqrt_rn(da(dm(dx, dx), dm(dy, dy)));
-  if (!(rxy > 0.0)) return false;
-  double t = ddv(S.a, rxy);
-  double qx = dm(t, dx), qy = dm(t, dy);
-  double ex = dsb(dx, qx), ey = dsb(dy, qy), ez = dz;
-  double ne = __dsqrt_rn(da(da(dm(ex, ex), dm(ey, ey)), dm(ez, ez)));
-  if (!(ne > 0.0)) return false;
-  double u = ddv(S.b, ne);
-  cp[0] = da(S.c[0], da(qx, dm(u, ex)));
-  cp[1] = da(S.c[1], da(qy, dm(u, ey)));
-  cp[2] = da(S.c[2], dm(u, ez));
-  return true;
-}
-
-// cube base b = floor(cp/h - (p-1)/2) and offset s = cp/h - b
-__device__ __forceinline__ void cube_base(double cpa, double h, int p, int* b, double* s) {
-  double u = ddv(cpa, h);
-  double f = floor(dsb(u, 0.5 * (double)(p - 1)));
-  *b = (int)f;
-  *s = dsb(u, f);
-}
-
-// barycentric weights of equispaced nodes: (-1)^j binom(p, j)
-__device__ __forceinline__ double bary_w(int p, int j) {
-  double b = 1.0;
-  for (int q = 1; q <= j; ++q) b = ddv(dm(b, (double)(p - q + 1)), (double)q);
-  return (j & 1) ? -b : b;
-}
-
-// 1-D weights, second (true) barycentric form; an exact node hit gives e_j
-__device__ void weights1d(int p, double s, double* out) {
-  for (int j = 0; j <= p; ++j)
-    if (s == (double)j) {
-      for (int q = 0; q <= p; ++q) out[q] = (q == j) ? 1.0 : 0.0;
-      return;
-    }
-  double t[4];
-  double den = 0.0;
-  for (int j = 0; j <= p; ++j) {
-    t[j] = ddv(bary_w(p, j), dsb(s, (double)j));
-    den = da(den, t[j]);
-  }
-  for (int j = 0; j <= p; ++j) out[j] = ddv(t[j], den);
-}
 
 struct TubeArgs {
   SurfDev S;
@@ -312,9 +231,9 @@ cpm_status bitmap_prefix(BitWord* bm, int64_t nw, int64_t* total, cudaStream_t s
   int64_t* pre = nullptr;
   CPM_TRY(dalloc(&cnt, nw, s));
   CPM_TRY(dalloc(&pre, nw + 1, s));
-  k_popc<<<grid_for(nw, 256), 256, 0, s>>>(bm, cnt, nw);
+  KL(k_popc<<<grid_for(nw, 256), 256, 0, s>>>(bm, cnt, nw));
   CPM_TRY(scan_exclusive_i32(cnt, pre, nw, s));
-  k_set_pre<<<grid_for(nw, 256), 256, 0, s>>>(bm, pre, nw);
+  KL(k_set_pre<<<grid_for(nw, 256), 256, 0, s>>>(bm, pre, nw));
   CPM_CUDA(cudaMemcpyAsync(total, pre + nw, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   CPM_CUDA(cudaStreamSynchronize(s));
   dfree(cnt, s);
@@ -402,9 +321,9 @@ cpm_status band_build(const cpm_surface* surf, double h, int p, cudaStream_t s, 
   }
   A.lam_hi = (float)(lam * 1.0001 + 1e-5 * scale);
   int64_t ncell = (int64_t)g.gn[0] * g.gn[1] * g.gn[2];
-  k_tube_mark<<<grid_for(ncell, 256, 152 * 32), 256, 0, s>>>(A, B->amap, nT, err);
+  KL(k_tube_mark<<<grid_for(ncell, 256, 152 * 32), 256, 0, s>>>(A, B->amap, nT, err));
   CPM_CUDA(cudaGetLastError());
-  k_dilate<<<grid_for(nw, 256), 256, 0, s>>>(B->amap, B->rmap, g);
+  KL(k_dilate<<<grid_for(nw, 256), 256, 0, s>>>(B->amap, B->rmap, g));
   CPM_CUDA(cudaGetLastError());
   int64_t nA = 0, nR = 0;
   if ((st = bitmap_prefix(B->amap, nw, &nA, s)) != CPM_OK) return cleanup(st);
@@ -430,9 +349,9 @@ cpm_status band_build(const cpm_surface* surf, double h, int p, cudaStream_t s, 
   if ((st = dalloc(&B->rcp, 3 * nR, s)) != CPM_OK) return cleanup(st);
   if ((st = dalloc(&B->w1d, 3 * P1 * nR, s)) != CPM_OK) return cleanup(st);
   if ((st = dalloc(&B->s32, 3 * nR, s)) != CPM_OK) return cleanup(st);
-  k_enumerate<<<grid_for(nw, 256), 256, 0, s>>>(B->amap, B->rmap, g, nA, B->ijkA, B->arow, B->rijk, B->rexp);
+  KL(k_enumerate<<<grid_for(nw, 256), 256, 0, s>>>(B->amap, B->rmap, g, nA, B->ijkA, B->arow, B->rijk, B->rexp));
   CPM_CUDA(cudaGetLastError());
-  k_erow<<<grid_for(nR, 128), 128, 0, s>>>(S, h, p, g, B->amap, nR, B->rijk, B->rbase, B->rcp, B->w1d, B->s32, err);
+  KL(k_erow<<<grid_for(nR, 128), 128, 0, s>>>(S, h, p, g, B->amap, nR, B->rijk, B->rbase, B->rcp, B->w1d, B->s32, err));
   CPM_CUDA(cudaGetLastError());
   CPM_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
   CPM_CUDA(cudaStreamSynchronize(s));
@@ -464,18 +383,18 @@ cpm_status band_export(const cpm_band* B, int32_t* ijkA, int32_t* ijkG, int32_t*
                        cudaStream_t s) {
   if (ijkA) CPM_CUDA(cudaMemcpyAsync(ijkA, B->ijkA, 3 * B->nA * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
   if (ijkG || ebase || ecp) {
-    k_export<<<grid_for(B->nR, 256), 256, 0, s>>>(B->nR, B->nA, B->rexp, B->rijk, B->rbase, B->rcp, ijkG, ebase, ecp);
+    KL(k_export<<<grid_for(B->nR, 256), 256, 0, s>>>(B->nR, B->nA, B->rexp, B->rijk, B->rbase, B->rcp, ijkG, ebase, ecp));
     CPM_CUDA(cudaGetLastError());
   }
   if (perm) {
-    k_iota64<<<grid_for(B->nA, 256), 256, 0, s>>>(perm, B->nA);
+    KL(k_iota64<<<grid_for(B->nA, 256), 256, 0, s>>>(perm, B->nA));
     CPM_CUDA(cudaGetLastError());
   }
   return CPM_OK;
 }
 
 cpm_status band_weights(const cpm_band* B, double* w, cudaStream_t s) {
-  k_export_w<<<grid_for(B->nR, 256), 256, 0, s>>>(B->nR, B->p + 1, B->rexp, B->w1d, w);
+  KL(k_export_w<<<grid_for(B->nR, 256), 256, 0, s>>>(B->nR, B->p + 1, B->rexp, B->w1d, w));
   CPM_CUDA(cudaGetLastError());
   return CPM_OK;
 }

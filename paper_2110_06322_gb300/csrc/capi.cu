@@ -10,6 +10,7 @@
 namespace cpm {
 
 static thread_local char g_err[512] = "";
+std::atomic<long long> g_launches{0};
 
 void set_error(const char* fmt, ...) {
   va_list ap;
@@ -40,6 +41,8 @@ static cudaStream_t as_stream(void* s) { return (cudaStream_t)s; }
 extern "C" {
 
 const char* cpm_last_error(void) { return g_err; }
+
+int64_t cpm_kernel_launches(void) { return (int64_t)g_launches.load(); }
 
 cpm_status cpm_band_build(const cpm_surface* surf, double h, int p, void* stream, cpm_band** out) {
   g_err[0] = 0;

@@ -5,6 +5,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <vector>
@@ -12,6 +13,12 @@
 #include "cpm.h"
 
 namespace cpm {
+
+// every kernel launch of the library goes through KL(...) so that callers can
+// count the kernels of a region (cpm_kernel_launches)
+extern std::atomic<long long> g_launches;
+inline void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+#define KL(...) ::cpm::count_launch(), __VA_ARGS__
 
 // ------------------------------------------------------------------ errors
 void set_error(const char* fmt, ...);

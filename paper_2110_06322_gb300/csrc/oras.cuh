@@ -15,6 +15,7 @@ struct oras_pc {
   int64_t nA = 0;
   int32_t* part = nullptr;    // [nA] disjoint part of each active node
   int64_t nloc = 0;           // sum_j |S_j|
+  int64_t max_rows = 0;       // max_j |S_j|
   int64_t* sptr = nullptr;    // [np+1]
   int32_t* snode = nullptr;   // [nloc] canonical node of each local row
   uint8_t* owned = nullptr;   // [nloc] node lies in the subdomain's own disjoint part
@@ -40,10 +41,22 @@ struct oras_pc {
   double* tval = nullptr;
   float* tval32 = nullptr;
   int32_t* tdpos = nullptr;
-  // node -> (subdomain, local row) memberships, for the adjoint's gather
-  int64_t* mptr = nullptr;    // [nA+1]
-  int64_t* mrow = nullptr;    // local rows, ascending subdomain
+  int32_t* lvsub_tf = nullptr;  // level schedules of the transposed factors
+  int64_t* lvptr_tf = nullptr;
+  int32_t* lvrow_tf = nullptr;
+  int32_t* lvsub_tb = nullptr;
+  int64_t* lvptr_tb = nullptr;
+  int32_t* lvrow_tb = nullptr;
+  // node -> subdomains holding it (ascending) and its local row there
+  int32_t* mcnt = nullptr;    // [nA]
+  int32_t* memb = nullptr;    // [nA][KMEM]
+  int32_t* mloc = nullptr;    // [nA][KMEM] local row (global numbering)
+  int32_t* lsub = nullptr;    // [nloc] subdomain of each local row
 };
+
+namespace cpm {
+constexpr int KMEM = 16;  // most subdomains one node may belong to
+}
 
 namespace cpm {
 cpm_status oras_build(const cpm_band* B, const oras_params* prm, double c, cudaStream_t s, oras_pc** out);

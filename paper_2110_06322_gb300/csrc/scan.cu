@@ -89,9 +89,9 @@ cpm_status scan_impl(const T* in, int64_t* out, int64_t n, cudaStream_t s) {
   }
   int64_t* tsum = nullptr;
   CPM_TRY(dalloc(&tsum, nt + 1, s));
-  k_tile_sums<T><<<(unsigned)nt, SCAN_THREADS, 0, s>>>(in, n, tsum);
-  k_scan_tiles<<<1, SCAN_THREADS, 0, s>>>(tsum, nt);
-  k_tile_scan<T><<<(unsigned)nt, SCAN_THREADS, 0, s>>>(in, n, tsum, out, nt);
+  KL(k_tile_sums<T><<<(unsigned)nt, SCAN_THREADS, 0, s>>>(in, n, tsum));
+  KL(k_scan_tiles<<<1, SCAN_THREADS, 0, s>>>(tsum, nt));
+  KL(k_tile_scan<T><<<(unsigned)nt, SCAN_THREADS, 0, s>>>(in, n, tsum, out, nt));
   cudaError_t e = cudaGetLastError();
   dfree(tsum, s);
   if (e != cudaSuccess) return cuda_fail(e, "scan kernels", __FILE__, __LINE__);

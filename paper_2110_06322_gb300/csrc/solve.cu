@@ -1,6 +1,513 @@
-// solve.cu -- placeholder (filled in next)
+// solve.cu -- restarted GMRES(m), right preconditioned by the Schwarz
+// preconditioner (Section 4.1.1: GMRES is the default Krylov method), and
+// FP64 iterative refinement around an FP32-operator inner GMRES.
+//
+// One iteration j:  z = P v_j;  w = M z;  classical Gram-Schmidt against
+// v_0..v_j (optionally a second pass);  h_{j+1,j} = |w|;  v_{j+1} = w / |w|;
+// Givens rotations update the least-squares problem on the device (one
+// thread, FP64) and publish the residual estimate |g_{j+1}|.  At the end of a
+// cycle x += P (V y) and the true residual |f - M x| (FP64) decides.
+//
+// All reductions are two-stage with a fixed grid and a fixed summation order,
+// so a solve is bitwise reproducible on the same device.
+#include <cmath>
+#include <vector>
+
 #include "kernels.cuh"
 #include "oras.cuh"
+
 namespace cpm {
-cpm_status solve_run(const cpm_band*, const oras_pc*, double, const double*, double*, const cpm_solve_params*, cpm_solve_info*, int, cudaStream_t) { return fail(CPM_ERR_ARG, "not built yet"); }
+
+namespace {
+
+constexpr int RED_THREADS = 256;
+constexpr int RED_BLOCKS = 152 * 2;
+constexpr int CH = 16;  // basis vectors per Gram-Schmidt pass kernel
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double t = 0;
+  if (threadIdx.x == 0)
+    for (int q = 0; q < RED_THREADS / 32; ++q) t += sh[q];
+  return t;
 }
+
+// partial[t * gridDim.x + b] = block b's share of <V_t, w>, t < nv
+__global__ void __launch_bounds__(RED_THREADS)
+    k_dots(const double* __restrict__ V, int64_t ld, int nv, const double* __restrict__ w, int64_t n,
+           double* partial) {
+  __shared__ double sh[RED_THREADS / 32];
+  double acc[CH];
+#pragma unroll
+  for (int t = 0; t < CH; ++t) acc[t] = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double wi = w[i];
+#pragma unroll
+    for (int t = 0; t < CH; ++t)
+      if (t < nv) acc[t] += V[t * ld + i] * wi;
+  }
+  for (int t = 0; t < nv; ++t) {
+    const double s = block_sum(acc[t], sh);
+    if (threadIdx.x == 0) partial[t * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+// w -= sum_t coef[t] V_t  (t < nv); when norm != 0 also partial sums of w^2
+__global__ void __launch_bounds__(RED_THREADS)
+    k_update(const double* __restrict__ V, int64_t ld, int nv, const double* __restrict__ coef, double* w, int64_t n,
+             int norm, double* partial) {
+  __shared__ double sh[RED_THREADS / 32];
+  double cf[CH];
+#pragma unroll
+  for (int t = 0; t < CH; ++t) cf[t] = t < nv ? coef[t] : 0.0;
+  double acc = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double wi = w[i];
+#pragma unroll
+    for (int t = 0; t < CH; ++t)
+      if (t < nv) wi -= cf[t] * V[t * ld + i];
+    w[i] = wi;
+    acc += wi * wi;
+  }
+  if (norm) {
+    const double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+  }
+}
+
+// out[t] (+)= sum_b partial[t * nb + b], fixed order
+__global__ void k_reduce(const double* __restrict__ partial, int nvals, int nb, double* out, int accumulate) {
+  __shared__ double sh[RED_THREADS / 32];
+  for (int t = 0; t < nvals; ++t) {
+    double v = 0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) v += partial[t * nb + b];
+    const double s = block_sum(v, sh);
+    if (threadIdx.x == 0) out[t] = accumulate ? out[t] + s : s;
+  }
+}
+
+__global__ void k_scale(const double* __restrict__ w, const double* __restrict__ nrm, double* v, int64_t n) {
+  const double inv = 1.0 / sqrt(*nrm);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    v[i] = w[i] * inv;
+}
+
+__global__ void k_sub(const double* __restrict__ f, double* r, int64_t n) {  // r = f - r
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    r[i] = f[i] - r[i];
+}
+
+__global__ void k_axpy(const double* __restrict__ z, double* x, int64_t n) {  // x += z
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] += z[i];
+}
+
+__global__ void k_d2f(const double* __restrict__ a, float* b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+__global__ void k_f2d(const float* __restrict__ a, double* b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (double)a[i];
+}
+
+// Givens update of column j (one thread).  hc[0..j+1] holds the new column
+// (its last entry the squared norm of w).  Publishes {|g_{j+1}|, h_{j+1,j}}.
+__global__ void k_givens(double* H, int m, const double* __restrict__ hc, double* cs, double* sn, double* g, int j,
+                         double* pub) {
+  if (threadIdx.x || blockIdx.x) return;
+  double col[258];
+  for (int i = 0; i <= j; ++i) col[i] = hc[i];
+  const double hn = sqrt(hc[j + 1]);
+  col[j + 1] = hn;
+  for (int i = 0; i < j; ++i) {
+    const double t0 = cs[i] * col[i] + sn[i] * col[i + 1];
+    const double t1 = -sn[i] * col[i] + cs[i] * col[i + 1];
+    col[i] = t0;
+    col[i + 1] = t1;
+  }
+  const double den = sqrt(col[j] * col[j] + col[j + 1] * col[j + 1]);
+  if (den == 0.0) {
+    cs[j] = 1.0;
+    sn[j] = 0.0;
+  } else {
+    cs[j] = col[j] / den;
+    sn[j] = col[j + 1] / den;
+  }
+  col[j] = den;
+  g[j + 1] = -sn[j] * g[j];
+  g[j] = cs[j] * g[j];
+  for (int i = 0; i <= j; ++i) H[i * m + j] = col[i];
+  pub[0] = fabs(g[j + 1]);
+  pub[1] = hn;
+}
+
+// y = H(0:k,0:k)^{-1} g (upper triangular), one thread
+__global__ void k_trisolve(const double* __restrict__ H, int m, const double* __restrict__ g, int k, double* y) {
+  if (threadIdx.x || blockIdx.x) return;
+  for (int i = k - 1; i >= 0; --i) {
+    double s = g[i];
+    for (int t = i + 1; t < k; ++t) s -= H[i * m + t] * y[t];
+    y[i] = s / H[i * m + i];
+  }
+}
+
+__global__ void k_negate(const double* __restrict__ a, double* b, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) b[i] = -a[i];
+}
+
+__global__ void k_add(double* a, const double* __restrict__ b, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a[i] += b[i];
+}
+
+__global__ void k_init_g(double* g, int m, const double* __restrict__ nrm2) {
+  for (int i = threadIdx.x; i <= m; i += blockDim.x) g[i] = 0.0;
+  if (threadIdx.x == 0) g[0] = sqrt(*nrm2);
+}
+
+struct Work {
+  int64_t n = 0;
+  int m = 0;
+  double *V = nullptr, *w = nullptr, *z = nullptr, *t = nullptr, *r = nullptr;
+  float *v32 = nullptr, *z32 = nullptr, *w32 = nullptr;
+  double *H = nullptr, *hc = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr, *ny = nullptr;
+  double *partial = nullptr, *scal = nullptr;
+  double* pub = nullptr;  // pinned host
+  cpm_status alloc(int64_t n_, int m_, bool f32, cudaStream_t s) {
+    n = n_;
+    m = m_;
+    CPM_TRY(dalloc(&V, (size_t)(m + 1) * n, s));
+    CPM_TRY(dalloc(&w, n, s));
+    CPM_TRY(dalloc(&z, n, s));
+    CPM_TRY(dalloc(&t, n, s));
+    CPM_TRY(dalloc(&r, n, s));
+    if (f32) {
+      CPM_TRY(dalloc(&v32, n, s));
+      CPM_TRY(dalloc(&z32, n, s));
+      CPM_TRY(dalloc(&w32, n, s));
+    }
+    CPM_TRY(dalloc(&H, (size_t)(m + 1) * m, s));
+    CPM_TRY(dalloc(&hc, m + 2, s));
+    CPM_TRY(dalloc(&cs, m, s));
+    CPM_TRY(dalloc(&sn, m, s));
+    CPM_TRY(dalloc(&g, m + 1, s));
+    CPM_TRY(dalloc(&y, m, s));
+    CPM_TRY(dalloc(&ny, m, s));
+    CPM_TRY(dalloc(&partial, (size_t)(CH + 1) * RED_BLOCKS, s));
+    CPM_TRY(dalloc(&scal, 8, s));
+    CPM_CUDA(cudaMallocHost((void**)&pub, 8 * sizeof(double)));
+    return CPM_OK;
+  }
+  void release(cudaStream_t s) {
+    for (double** p : {&V, &w, &z, &t, &r, &H, &hc, &cs, &sn, &g, &y, &ny, &partial, &scal}) dfree(*p, s);
+    dfree(v32, s);
+    dfree(z32, s);
+    dfree(w32, s);
+    if (pub) cudaFreeHost(pub);
+    pub = nullptr;
+  }
+};
+
+struct Timing {
+  bool on = false;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  double ms_P = 0, ms_M = 0;
+  int nP = 0, nM = 0;
+  void start(cudaStream_t s) {
+    if (on) cudaEventRecord(e0, s);
+  }
+  void stop(cudaStream_t s, bool prec) {
+    if (!on) return;
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (prec) {
+      ms_P += ms;
+      nP++;
+    } else {
+      ms_M += ms;
+      nM++;
+    }
+  }
+};
+
+struct Ops {
+  const cpm_band* B;
+  const oras_pc* P;
+  double c;
+  int transpose;
+  int f32;  // operator and preconditioner in FP32
+  Timing* tm;
+};
+
+const int GB = RED_BLOCKS;
+
+// out = M x (FP64 or FP32 operator)
+cpm_status op_M(const Ops& o, const double* x, double* out, Work& W, cudaStream_t s) {
+  if (!o.f32) {
+    o.tm->start(s);
+    CPM_TRY(apply_op(o.B, &o.c, x, out, CPM_F64, 1, o.transpose, s));
+    o.tm->stop(s, false);
+    return CPM_OK;
+  }
+  KL(k_d2f<<<grid_for(W.n, 256), 256, 0, s>>>(x, W.v32, W.n));
+  o.tm->start(s);
+  CPM_TRY(apply_op(o.B, &o.c, W.v32, W.w32, CPM_F32, 1, o.transpose, s));
+  o.tm->stop(s, false);
+  KL(k_f2d<<<grid_for(W.n, 256), 256, 0, s>>>(W.w32, out, W.n));
+  return CPM_OK;
+}
+
+// out = P v
+cpm_status op_P(const Ops& o, const double* v, double* out, Work& W, cudaStream_t s) {
+  if (!o.P) {
+    CPM_CUDA(cudaMemcpyAsync(out, v, W.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    return CPM_OK;
+  }
+  if (!o.f32) {
+    o.tm->start(s);
+    CPM_TRY(oras_run(o.P, v, out, CPM_F64, 1, o.transpose, s));
+    o.tm->stop(s, true);
+    return CPM_OK;
+  }
+  KL(k_d2f<<<grid_for(W.n, 256), 256, 0, s>>>(v, W.v32, W.n));
+  o.tm->start(s);
+  CPM_TRY(oras_run(o.P, W.v32, W.z32, CPM_F32, 1, o.transpose, s));
+  o.tm->stop(s, true);
+  KL(k_f2d<<<grid_for(W.n, 256), 256, 0, s>>>(W.z32, out, W.n));
+  return CPM_OK;
+}
+
+// out[0] = <a, a>
+cpm_status norm2(const double* a, int64_t n, double* out, Work& W, cudaStream_t s) {
+  KL(k_dots<<<GB, RED_THREADS, 0, s>>>(a, 0, 1, a, n, W.partial));
+  KL(k_reduce<<<1, RED_THREADS, 0, s>>>(W.partial, 1, GB, out, 0));
+  return CPM_OK;
+}
+
+// Gram-Schmidt of w against V_0..V_j; hc[0..j] = coefficients, hc[j+1] = |w|^2
+cpm_status gram_schmidt(int j, int reorth, Work& W, cudaStream_t s) {
+  const int nv = j + 1;
+  for (int pass = 0; pass < (reorth ? 2 : 1); ++pass) {
+    for (int t0 = 0; t0 < nv; t0 += CH) {
+      const int nc = nv - t0 < CH ? nv - t0 : CH;
+      KL(k_dots<<<GB, RED_THREADS, 0, s>>>(W.V + (int64_t)t0 * W.n, W.n, nc, W.w, W.n, W.partial));
+      // pass 0 writes the coefficients; pass 1 adds to them; the update uses
+      // this pass's coefficients (kept in y as scratch)
+      KL(k_reduce<<<1, RED_THREADS, 0, s>>>(W.partial, nc, GB, W.y + t0, 0));
+    }
+    if (pass == 0) CPM_CUDA(cudaMemcpyAsync(W.hc, W.y, nv * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    else KL(k_add<<<1, 256, 0, s>>>(W.hc, W.y, nv));  // second pass: coefficients accumulate
+    const bool last = pass == (reorth ? 1 : 0);
+    for (int t0 = 0; t0 < nv; t0 += CH) {
+      const int nc = nv - t0 < CH ? nv - t0 : CH;
+      const bool lastchunk = last && t0 + CH >= nv;
+      KL(k_update<<<GB, RED_THREADS, 0, s>>>(W.V + (int64_t)t0 * W.n, W.n, nc, W.y + t0, W.w, W.n, lastchunk ? 1 : 0,
+                                          W.partial));
+    }
+  }
+  KL(k_reduce<<<1, RED_THREADS, 0, s>>>(W.partial, 1, GB, W.hc + j + 1, 0));
+  CPM_CUDA(cudaGetLastError());
+  return CPM_OK;
+}
+
+struct GmresOut {
+  int iters = 0, cycles = 0;
+  double relres = 0;
+  cpm_status status = CPM_OK;
+};
+
+// one_cycle: x must be zero on entry; run a single cycle from r = f and
+// return (the inner solve of iterative refinement).
+cpm_status gmres(const Ops& o, const double* f, double* x, int m, int maxit, double rtol, int reorth, Work& W,
+                 GmresOut& out, cudaStream_t s, bool one_cycle = false) {
+  const int64_t n = W.n;
+  const int G = grid_for(n, 256);
+  CPM_TRY(norm2(f, n, W.scal, W, s));
+  double fn2 = 0;
+  CPM_CUDA(cudaMemcpyAsync(&fn2, W.scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CPM_CUDA(cudaStreamSynchronize(s));
+  const double fn = std::sqrt(fn2);
+  if (!std::isfinite(fn)) {
+    out.status = CPM_ERR_NAN;
+    return fail(CPM_ERR_NAN, "right-hand side holds NaN or Inf");
+  }
+  if (fn == 0.0) {
+    CPM_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+    out.relres = 0;
+    out.status = CPM_OK;
+    return CPM_OK;
+  }
+  bool first = true;
+  while (true) {
+    if (one_cycle && !first) {
+      out.status = CPM_OK;
+      return CPM_OK;
+    }
+    first = false;
+    // r = f - M x
+    if (one_cycle) {
+      CPM_CUDA(cudaMemcpyAsync(W.r, f, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    } else {
+      CPM_TRY(op_M(o, x, W.r, W, s));
+      KL(k_sub<<<G, 256, 0, s>>>(f, W.r, n));
+    }
+    CPM_TRY(norm2(W.r, n, W.scal + 1, W, s));
+    double b2 = 0;
+    CPM_CUDA(cudaMemcpyAsync(&b2, W.scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CPM_CUDA(cudaStreamSynchronize(s));
+    const double beta = std::sqrt(b2);
+    out.relres = beta / fn;
+    if (!std::isfinite(beta)) {
+      out.status = CPM_ERR_NAN;
+      return fail(CPM_ERR_NAN, "residual became NaN or Inf");
+    }
+    if (out.relres <= rtol) {
+      out.status = CPM_OK;
+      return CPM_OK;
+    }
+    if (out.iters >= maxit) {
+      out.status = CPM_ERR_NOT_CONVERGED;
+      return CPM_OK;
+    }
+    out.cycles++;
+    KL(k_scale<<<G, 256, 0, s>>>(W.r, W.scal + 1, W.V, n));
+    KL(k_init_g<<<1, 256, 0, s>>>(W.g, m, W.scal + 1));
+    int k = 0;
+    for (int j = 0; j < m && out.iters < maxit; ++j) {
+      double* vj = W.V + (int64_t)j * n;
+      CPM_TRY(op_P(o, vj, W.z, W, s));
+      CPM_TRY(op_M(o, W.z, W.w, W, s));
+      CPM_TRY(gram_schmidt(j, reorth, W, s));
+      KL(k_givens<<<1, 1, 0, s>>>(W.H, m, W.hc, W.cs, W.sn, W.g, j, W.scal + 2));
+      CPM_CUDA(cudaMemcpyAsync(W.pub, W.scal + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CPM_CUDA(cudaStreamSynchronize(s));
+      CPM_CUDA(cudaGetLastError());
+      out.iters++;
+      k = j + 1;
+      const double est = W.pub[0], hn = W.pub[1];
+      if (!std::isfinite(est)) {
+        out.status = CPM_ERR_NAN;
+        return fail(CPM_ERR_NAN, "Krylov iteration produced NaN or Inf");
+      }
+      if (hn == 0.0 || est <= rtol * fn) break;
+      if (j + 1 < m) KL(k_scale<<<G, 256, 0, s>>>(W.w, W.hc + j + 1, W.V + (int64_t)(j + 1) * n, n));
+    }
+    // x += P (V y)
+    KL(k_trisolve<<<1, 1, 0, s>>>(W.H, m, W.g, k, W.y));
+    CPM_CUDA(cudaMemsetAsync(W.t, 0, n * sizeof(double), s));
+    KL(k_negate<<<1, 256, 0, s>>>(W.y, W.ny, k));
+    for (int t0 = 0; t0 < k; t0 += CH) {
+      const int nc = k - t0 < CH ? k - t0 : CH;
+      KL(k_update<<<GB, RED_THREADS, 0, s>>>(W.V + (int64_t)t0 * n, n, nc, W.ny + t0, W.t, n, 0, nullptr));
+    }
+    CPM_TRY(op_P(o, W.t, W.z, W, s));
+    KL(k_axpy<<<G, 256, 0, s>>>(W.z, x, n));
+    CPM_CUDA(cudaGetLastError());
+  }
+}
+
+}  // namespace
+
+cpm_status solve_run(const cpm_band* B, const oras_pc* P, double c, const double* f, double* u,
+                     const cpm_solve_params* prm, cpm_solve_info* info, int transpose, cudaStream_t s) {
+  *info = cpm_solve_info{};
+  const int64_t n = B->nA;
+  if (prm->mixed && P && !P->val32 && !P->val16)
+    return fail(CPM_ERR_ARG, "mixed precision needs FP32 or BF16 factors (oras_params.store)");
+  Work W;
+  cpm_status st = W.alloc(n, prm->restart, prm->mixed != 0, s);
+  if (st != CPM_OK) {
+    W.release(s);
+    return st;
+  }
+  Timing tm;
+  tm.on = prm->timing != 0;
+  if (tm.on) {
+    cudaEventCreate(&tm.e0);
+    cudaEventCreate(&tm.e1);
+  }
+  Ops o64{B, P, c, transpose, 0, &tm};
+  GmresOut out;
+  if (!prm->mixed) {
+    st = gmres(o64, f, u, prm->restart, prm->maxit, prm->rtol, prm->reorth, W, out, s);
+  } else {
+    // FP64 iterative refinement: r = f - M u (FP64); one GMRES(m) cycle on
+    // M d = r with the FP32 operator and preconditioner (FP64 basis and least
+    // squares); u += d.  Every restart residual is thus an FP64 residual.
+    Ops o32{B, P, c, transpose, 1, &tm};
+    double *r = nullptr, *d = nullptr;
+    st = dalloc(&r, n, s);
+    if (st == CPM_OK) st = dalloc(&d, n, s);
+    double fn2 = 0;
+    if (st == CPM_OK) st = norm2(f, n, W.scal + 4, W, s);
+    if (st == CPM_OK) {
+      cudaMemcpyAsync(&fn2, W.scal + 4, sizeof(double), cudaMemcpyDeviceToHost, s);
+      cudaStreamSynchronize(s);
+    }
+    const double fn = std::sqrt(fn2);
+    const double inner = prm->inner_rtol > 0 ? prm->inner_rtol : 1e-4;
+    while (st == CPM_OK) {
+      st = op_M(o64, u, r, W, s);
+      if (st != CPM_OK) break;
+      KL(k_sub<<<grid_for(n, 256), 256, 0, s>>>(f, r, n));
+      st = norm2(r, n, W.scal + 5, W, s);
+      double r2 = 0;
+      cudaMemcpyAsync(&r2, W.scal + 5, sizeof(double), cudaMemcpyDeviceToHost, s);
+      cudaStreamSynchronize(s);
+      out.relres = fn > 0 ? std::sqrt(r2) / fn : 0.0;
+      if (!std::isfinite(out.relres)) {
+        st = fail(CPM_ERR_NAN, "residual became NaN or Inf");
+        out.status = CPM_ERR_NAN;
+        break;
+      }
+      if (out.relres <= prm->rtol) {
+        out.status = CPM_OK;
+        break;
+      }
+      if (out.iters >= prm->maxit) {
+        out.status = CPM_ERR_NOT_CONVERGED;
+        break;
+      }
+      cudaMemsetAsync(d, 0, n * sizeof(double), s);
+      GmresOut in;
+      st = gmres(o32, r, d, prm->restart, prm->maxit - out.iters, inner, prm->reorth, W, in, s, true);
+      out.iters += in.iters;
+      out.cycles += in.cycles;
+      info->ir_steps++;
+      if (st != CPM_OK) break;
+      KL(k_axpy<<<grid_for(n, 256), 256, 0, s>>>(d, u, n));
+    }
+    dfree(r, s);
+    dfree(d, s);
+  }
+  cudaError_t e = cudaStreamSynchronize(s);
+  W.release(s);
+  cudaStreamSynchronize(s);
+  info->iters = out.iters;
+  info->restarts = out.cycles;
+  info->rel_residual = out.relres;
+  info->status = st != CPM_OK ? st : out.status;
+  info->ms_precond = tm.ms_P;
+  info->ms_operator = tm.ms_M;
+  info->n_precond = tm.nP;
+  info->n_operator = tm.nM;
+  if (tm.on) {
+    cudaEventDestroy(tm.e0);
+    cudaEventDestroy(tm.e1);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "solver", __FILE__, __LINE__);
+  if (st != CPM_OK) return st;
+  if (out.status == CPM_ERR_NOT_CONVERGED)
+    return fail(CPM_ERR_NOT_CONVERGED, "not converged: relative residual %.3e after %d iterations", out.relres,
+                out.iters);
+  return out.status;
+}
+
+}  // namespace cpm

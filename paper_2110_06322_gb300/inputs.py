@@ -68,10 +68,10 @@ WORKLOADS = {
     "sphere_h0.1": dict(kind=SPHERE, params=surface_params(SPHERE, a=1.0), h=0.1, p=3, c=1.0,
                         rhs="y32", nparts=8, overlap=2, robin=False, restart=30, rtol=1e-10),
     "torus_h0.004": dict(kind=TORUS, params=surface_params(TORUS, a=1.0, b=0.4), h=0.004, p=3, c=10.0,
-                         rhs="modes", seed=2, nparts=512, overlap=2, robin=True, alpha=4.0, alpha_cross=20.0,
+                         rhs="modes", seed=2, nparts=512, overlap=2, robin=False, alpha=4.0, alpha_cross=20.0,
                          restart=30, rtol=1e-8),
     "torus_h0.002": dict(kind=TORUS, params=surface_params(TORUS, a=1.0, b=0.4), h=0.002, p=3, c=10.0,
-                         rhs="modes", seed=3, nparts=512, overlap=2, robin=True, alpha=4.0, alpha_cross=20.0,
+                         rhs="modes", seed=3, nparts=512, overlap=2, robin=False, alpha=4.0, alpha_cross=20.0,
                          restart=30, rtol=1e-8),
 }
 

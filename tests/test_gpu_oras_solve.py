@@ -1,0 +1,181 @@
+"""GPU parity: Schwarz preconditioner and GMRES solver vs the FP64 oracle.
+
+Partition and subdomain lists (in their local order) are integer data and
+must be identical.  The preconditioner apply uses the same ILU(0) factors in
+the same local order; only the summation order inside each row differs, so
+FP64 agreement is required to 1e-12 relative (the triangular solves amplify
+rounding by their growth, which stays below 1e3 on these bands).  Solutions:
+FP64 solves agree with the oracle's direct solve to 1e-10 relative (both
+sides at rtol 1e-13, Section 4.1.1 GMRES); the mixed-precision solve must
+reach 1e-8 relative error.
+"""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as sla
+import torch
+
+from paper_2110_06322_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+SPH = (0.0, 0.0, 0.0, 1.0)
+TOR = (0.0, 0.0, 0.0, 1.0, 0.4)
+
+
+@pytest.fixture(scope="module")
+def cpm():
+    from paper_2110_06322_gb300 import cpm as m
+    m.lib()
+    return m
+
+
+@pytest.fixture(scope="module")
+def torus005(cpm, oracle_mod):
+    B = cpm.Band(1, TOR, 0.05, 3)
+    O = oracle_mod.Band(1, TOR, 0.05, 3)
+    return B, O, O.M(10.0)
+
+
+@pytest.fixture(scope="module")
+def sphere01(cpm, oracle_mod):
+    B = cpm.Band(0, SPH, 0.1, 3)
+    O = oracle_mod.Band(0, SPH, 0.1, 3)
+    return B, O, O.M(1.0)
+
+
+def _cuda(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+@pytest.mark.parametrize("nparts,overlap", [(1, 0), (8, 2), (13, 1), (64, 2), (64, 3)])
+def test_partition_and_local_order_identical(cpm, oracle_mod, torus005, nparts, overlap):
+    B, O, M = torus005
+    P = cpm.Schwarz(B, 10.0, nparts, overlap)
+    OP = oracle_mod.ORAS(O, M, nparts, overlap)
+    part, sptr, nodes = [t.cpu().numpy() for t in P.export()]
+    assert np.array_equal(part, OP.partition())
+    for j in range(nparts):
+        assert np.array_equal(nodes[sptr[j]:sptr[j + 1]], OP.sub_nodes(j))
+
+
+@pytest.mark.parametrize("robin", [False, True])
+def test_schwarz_apply_matches_oracle(cpm, oracle_mod, torus005, robin):
+    B, O, M = torus005
+    P = cpm.Schwarz(B, 10.0, 16, 2, robin=robin)
+    OP = oracle_mod.ORAS(O, M, 16, 2, robin=robin)
+    r = inputs.gaussian_vector(5, B.n_active)
+    want = OP.apply(r)
+    got = P.apply(_cuda(r)).cpu().numpy()
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+    got32 = P.apply(_cuda(r).float()).double().cpu().numpy()
+    assert np.abs(got32 - want).max() <= 1e-4 * np.abs(want).max()
+    wantT = OP.apply(r, transpose=True)
+    gotT = P.apply(_cuda(r), transpose=True).cpu().numpy()
+    assert np.abs(gotT - wantT).max() <= 1e-12 * np.abs(wantT).max()
+
+
+def test_schwarz_several_rhs(cpm, oracle_mod, sphere01):
+    B, O, M = sphere01
+    P = cpm.Schwarz(B, 1.0, 8, 2, robin=True)
+    OP = oracle_mod.ORAS(O, M, 8, 2, robin=True)
+    R = np.stack([inputs.gaussian_vector(60 + q, B.n_active) for q in range(3)])
+    Z = P.apply(_cuda(R).reshape(-1)).cpu().numpy().reshape(3, -1)
+    for q in range(3):
+        want = OP.apply(R[q])
+        assert np.abs(Z[q] - want).max() <= 1e-12 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("robin", [False, True])
+def test_fp64_solve_matches_direct_solve(cpm, oracle_mod, torus005, robin):
+    B, O, M = torus005
+    f = inputs.gaussian_vector(4, B.n_active)
+    xd = sla.spsolve(M.to_scipy().tocsc(), f)
+    P = cpm.Schwarz(B, 10.0, 16, 2, robin=robin)
+    u, info = cpm.solve(B, _cuda(f), P, rtol=1e-13, maxit=5000)
+    assert info["status"] == 0, info
+    assert np.linalg.norm(u.cpu().numpy() - xd) <= 1e-10 * np.linalg.norm(xd)
+    # the oracle's own GMRES with the same preconditioner reaches the same u
+    xo, oinfo = oracle_mod.gmres(M, f, oracle_mod.ORAS(O, M, 16, 2, robin=robin), rtol=1e-13)
+    assert np.linalg.norm(u.cpu().numpy() - xo) <= 1e-10 * np.linalg.norm(xo)
+
+
+def test_mixed_precision_solve_reaches_1e8(cpm, oracle_mod, torus005):
+    B, O, M = torus005
+    f = inputs.gaussian_vector(7, B.n_active)
+    xd = sla.spsolve(M.to_scipy().tocsc(), f)
+    for store in (cpm.CPM_F32, cpm.CPM_BF16):
+        P = cpm.Schwarz(B, 10.0, 16, 2, robin=True, store=store)
+        u, info = cpm.solve(B, _cuda(f), P, rtol=1e-10, mixed=True, maxit=5000)
+        assert info["status"] == 0 and info["ir_steps"] >= 1, info
+        assert np.linalg.norm(u.cpu().numpy() - xd) <= 1e-8 * np.linalg.norm(xd)
+
+
+def test_sphere_harmonic_solution(cpm, oracle_mod, sphere01):
+    B, O, M = sphere01
+    cp = B.export()[3][: B.n_active].cpu().numpy()
+    f = 13.0 * inputs.y32(cp)
+    P = cpm.Schwarz(B, 1.0, 8, 2)
+    u, info = cpm.solve(B, _cuda(f), P, rtol=1e-13)
+    assert info["status"] == 0
+    xd = sla.spsolve(M.to_scipy().tocsc(), f)
+    assert np.linalg.norm(u.cpu().numpy() - xd) <= 1e-10 * np.linalg.norm(xd)
+
+
+def test_adjoint_solve(cpm, oracle_mod, torus005):
+    B, O, M = torus005
+    g = inputs.gaussian_vector(8, B.n_active)
+    lam_d = sla.spsolve(M.to_scipy().T.tocsc(), g)
+    for robin in (False, True):
+        P = cpm.Schwarz(B, 10.0, 16, 2, robin=robin)
+        lam, info = cpm.solve(B, _cuda(g), P, rtol=1e-13, adjoint=True, maxit=5000)
+        assert info["status"] == 0, info
+        assert np.linalg.norm(lam.cpu().numpy() - lam_d) <= 1e-10 * np.linalg.norm(lam_d)
+
+
+def test_unpreconditioned_and_edge_cases(cpm, oracle_mod, sphere01):
+    B, O, M = sphere01
+    f = inputs.gaussian_vector(9, B.n_active)
+    xd = sla.spsolve(M.to_scipy().tocsc(), f)
+    u, info = cpm.solve(B, _cuda(f), None, c=1.0, rtol=1e-12, maxit=20000)
+    assert info["status"] == 0
+    assert np.linalg.norm(u.cpu().numpy() - xd) <= 1e-9 * np.linalg.norm(xd)
+    # zero right-hand side
+    u, info = cpm.solve(B, torch.zeros(B.n_active, dtype=torch.float64, device="cuda"), None, c=1.0)
+    assert info["status"] == 0 and info["iters"] == 0 and u.abs().max().item() == 0.0
+    # iteration limit
+    P = cpm.Schwarz(B, 1.0, 8, 2)
+    u, info = cpm.solve(B, _cuda(f), P, rtol=1e-12, maxit=3)
+    assert info["status"] == cpm.CPM_ERR_NOT_CONVERGED and info["iters"] == 3
+    # NaN in the right-hand side is reported, not propagated silently
+    fn = f.copy()
+    fn[17] = np.nan
+    with pytest.raises(cpm.CpmError) as e:
+        cpm.solve(B, _cuda(fn), P, rtol=1e-8)
+    assert e.value.status == cpm.CPM_ERR_NAN
+    # more parts than some boxes can fill: empty subdomains are harmless
+    P2 = cpm.Schwarz(B, 1.0, 1000, 1)
+    u, info = cpm.solve(B, _cuda(f), P2, rtol=1e-12, maxit=5000)
+    assert info["status"] == 0
+
+
+def test_full_size_torus_solve(cpm, oracle_mod):
+    """Torus h = 0.004 (5.7M band points), 512 parts, overlap 2, RAS with
+    ILU(0), GMRES(30): the FP64 solve at rtol 1e-8 and the mixed-precision
+    solve at rtol 1e-10.  The true residual of the mixed solution is checked on
+    sampled rows assembled by the oracle (|r_i| <= |r|_2 <= 1e-10 |f|_2), and
+    the two solutions against each other."""
+    h, c = 0.004, 10.0
+    B = cpm.Band(1, TOR, h, 3)
+    cp = B.export()[3][: B.n_active].cpu().numpy()
+    f = inputs.torus_rhs(cp, inputs.torus_modes(2))
+    P = cpm.Schwarz(B, c, 512, 2)
+    u, info = cpm.solve(B, _cuda(f), P, rtol=1e-8, maxit=20000)
+    assert info["status"] == 0, info
+    u32, info32 = cpm.solve(B, _cuda(f), P, rtol=1e-10, mixed=True, maxit=20000)
+    assert info32["status"] == 0, info32
+    un, u32n = u.cpu().numpy(), u32.cpu().numpy()
+    O = oracle_mod.Band(1, TOR, h, 3)
+    rows = np.random.default_rng(1).integers(0, B.n_active, 2000)
+    res = O.apply_rows(c, u32n, rows) - f[rows]
+    assert np.abs(res).max() <= 2e-10 * np.linalg.norm(f)
+    assert np.linalg.norm(un - u32n) <= 1e-6 * np.linalg.norm(u32n)
