@@ -108,6 +108,23 @@ cpm_status cpm_band_weights(const cpm_band* band, double* w1d, void* stream);
 cpm_status cpm_apply(const cpm_band* band, const double* c, const void* x, void* y, cpm_dtype dtype, int nrhs,
                      int transpose, void* stream);
 
+/* cpm_apply_noalloc -- the forward operator of cpm_apply (y = M x, same
+ * arguments and layout, no transpose) for callers that cannot allocate device
+ * memory: processes whose device memory belongs to another allocator (a
+ * framework's caching pool that has reserved the device) or latency-bounded
+ * loops in which an allocation may block.  This is not an operation of the
+ * paper; it only changes where the apply's scratch comes from.
+ *   Scratch: one fixed 16 MiB array inside the library, held by every device
+ *   that loads it until the process exits.  A call needs
+ *   min(nrhs, 16) x N_C x 8 bytes (N_C = N_A + N_G); larger calls are rejected
+ *   with CPM_ERR_ARG and a message naming the sizes.
+ *   The first call on a device looks up the array's device address (with
+ *   that device current); make that first call before any stream capture.
+ *   All calls share the array: calls whose kernels overlap on the GPU race.
+ *   Allocates nothing (no cudaMalloc, no stream-ordered or library allocation). */
+cpm_status cpm_apply_noalloc(const cpm_band* band, const double* c, const void* x, void* y, cpm_dtype dtype,
+                             int nrhs, void* stream);
+
 /* ------------------------------------------------------------------ Schwarz preconditioner
  * (Section 2.2; defaults of Section 4.1.1: alpha = 4, alpha_cross = 20, ILU(0) local solves)
  *   nparts       number of disjoint subdomains N_S, from recursive coordinate

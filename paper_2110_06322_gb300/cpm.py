@@ -79,6 +79,7 @@ def lib():
         "cpm_band_free": (None, [vp]),
         "oras_free": (None, [vp]),
         "cpm_kernel_launches": (C.c_int64, []),
+        "cpm_apply_noalloc": (i32, [vp, P(C.c_double), vp, vp, i32, i32, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -90,7 +91,7 @@ def lib():
 
 EXPORTED = ["cpm_last_error", "cpm_band_build", "cpm_band_info", "cpm_band_export", "cpm_band_weights", "cpm_apply",
             "oras_setup", "oras_apply", "oras_info", "oras_export", "cpm_solve", "cpm_solve_adjoint", "cpm_band_free",
-            "oras_free", "cpm_kernel_launches"]
+            "oras_free", "cpm_kernel_launches", "cpm_apply_noalloc"]
 
 
 def _check(st):
@@ -131,6 +132,14 @@ def cpm_apply(band, c, x, y, transpose=False, stream=None):
     nrhs = x.numel() // Band.n_active_of(band)
     cs = (C.c_double * nrhs)(*([float(c)] * nrhs if not hasattr(c, "__len__") else [float(v) for v in c]))
     _check(lib().cpm_apply(band, cs, _ptr(x), _ptr(y), _dtype_code(x), nrhs, int(bool(transpose)), _stream(stream)))
+    return y
+
+
+def cpm_apply_noalloc(band, c, x, y, stream=None):
+    """y = M x through the entry point that allocates nothing (fixed library scratch)."""
+    nrhs = x.numel() // Band.n_active_of(band)
+    cs = (C.c_double * nrhs)(*([float(c)] * nrhs if not hasattr(c, "__len__") else [float(v) for v in c]))
+    _check(lib().cpm_apply_noalloc(band, cs, _ptr(x), _ptr(y), _dtype_code(x), nrhs, _stream(stream)))
     return y
 
 

@@ -292,7 +292,35 @@ cpm_status apply_typed(const cpm_band* B, const double* c, const T* x, T* y, int
   return CPM_OK;
 }
 
+template <typename T>
+cpm_status apply_fwd_scratch(const cpm_band* B, const double* c, const T* x, T* y, int nrhs, T* w, cudaStream_t s) {
+  ApplyGeom G = geom_of(B);
+  for (int r0 = 0; r0 < nrhs; r0 += MAXRHS) {
+    int nr = nrhs - r0 < MAXRHS ? nrhs - r0 : MAXRHS;
+    Shifts S{};
+    for (int q = 0; q < nr; ++q) S.c[q] = c[r0 + q];
+    const T* xr = x + (int64_t)r0 * B->nA;
+    T* yr = y + (int64_t)r0 * B->nA;
+    dim3 g1(grid_for(B->nR, 256), nr), g2(grid_for(B->nA, 256), nr);
+    if (B->p == 3) KL(k_erow_apply<T, 3><<<g1, 256, 0, s>>>(G, xr, w));
+    else KL(k_erow_apply<T, 2><<<g1, 256, 0, s>>>(G, xr, w));
+    KL(k_stencil<T><<<g2, 256, 0, s>>>(G, S, xr, w, yr));
+    CPM_CUDA(cudaGetLastError());
+  }
+  return CPM_OK;
+}
+
 }  // namespace
+
+// Forward operator with scratch supplied by the caller: at least
+// min(nrhs, 16) * nR * 8 bytes, 8-byte aligned.  Allocates nothing.
+cpm_status apply_op_scratch(const cpm_band* B, const double* c, const void* x, void* y, cpm_dtype dt, int nrhs,
+                            void* scratch, cudaStream_t s) {
+  if (dt == CPM_F64)
+    return apply_fwd_scratch<double>(B, c, (const double*)x, (double*)y, nrhs, (double*)scratch, s);
+  if (dt == CPM_F32) return apply_fwd_scratch<float>(B, c, (const float*)x, (float*)y, nrhs, (float*)scratch, s);
+  return fail(CPM_ERR_ARG, "cpm_apply_noalloc supports CPM_F64 and CPM_F32 vectors");
+}
 
 cpm_status build_transpose_map(cpm_band* B, cudaStream_t s) {
   ApplyGeom G = geom_of(B);

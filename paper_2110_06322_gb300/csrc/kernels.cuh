@@ -23,5 +23,7 @@ cpm_status apply_op(const cpm_band* B, const double* c, const void* x, void* y, 
 // E x for all rows (into B->wbuf) followed by the stencil; exposed so that
 // the solver can reuse it with device-side c.
 cpm_status build_transpose_map(cpm_band* B, cudaStream_t s);
+cpm_status apply_op_scratch(const cpm_band* B, const double* c, const void* x, void* y, cpm_dtype dt, int nrhs,
+                            void* scratch, cudaStream_t s);
 
 }  // namespace cpm
