@@ -627,15 +627,6 @@ __global__ void __launch_bounds__(ILU_WARPS * 32)
   }
 }
 
-__global__ void k_to_f32(int64_t n, const double* __restrict__ a, float* b) {
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
-    b[q] = (float)a[q];
-}
-__global__ void k_to_bf16(int64_t n, const double* __restrict__ a, __nv_bfloat16* b) {
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
-    b[q] = __float2bfloat16_rn((float)a[q]);
-}
-
 // ------------------------------------------------------------------ transposed factors
 __global__ void k_tcount_f(int64_t nloc, const int64_t* __restrict__ sptr, const int32_t* __restrict__ lsub,
                            const int64_t* __restrict__ rptr, const int32_t* __restrict__ col, int32_t* cnt) {
@@ -747,8 +738,6 @@ cpm_status oras_build_transpose(oras_pc* P, cudaStream_t s) {
   KL(k_tsort_f<<<G, 256, 0, s>>>(nloc, P->sptr, P->lsub, P->tptr, P->tcol, P->tval, P->tdpos));
   CPM_CUDA(cudaGetLastError());
   dfree(cnt, s);
-  CPM_TRY(dalloc(&P->tval32, P->nnz, s));
-  KL(k_to_f32<<<grid_for(P->nnz, 256), 256, 0, s>>>(P->nnz, P->tval, P->tval32));
   int32_t ml = 0;
   CPM_TRY(build_schedule(P, P->tptr, P->tcol, P->tdpos, 1, &P->lvsub_tf, &P->lvptr_tf, &P->lvrow_tf, &ml, s));
   CPM_TRY(build_schedule(P, P->tptr, P->tcol, P->tdpos, 0, &P->lvsub_tb, &P->lvptr_tb, &P->lvrow_tb, &ml, s));
@@ -926,13 +915,11 @@ cpm_status oras_build(const cpm_band* B, const oras_params* prm, double c, cudaS
   TRYC(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
   TRYC(cudaStreamSynchronize(s));
   if (herr) return cleanup(fail(CPM_ERR_BREAKDOWN, "zero pivot in the ILU(0) factorisation"));
-  if (P->store == CPM_F32) {
-    TRY(dalloc(&P->val32, P->nnz, s));
-    KL(k_to_f32<<<grid_for(P->nnz, 256), 256, 0, s>>>(P->nnz, P->val, P->val32));
-  } else if (P->store == CPM_BF16) {
-    TRY(dalloc(&P->val16, P->nnz, s));
-    KL(k_to_bf16<<<grid_for(P->nnz, 256), 256, 0, s>>>(P->nnz, P->val, P->val16));
-  }
+  // level-packed factors for the applies: FP64, and the stored precision
+  TRY(dalloc(&P->err, 1, s));
+  TRYC(cudaMemsetAsync(P->err, 0, sizeof(int), s));
+  TRY(pack_factors(P, 0, CPM_F64, P->packed[0], s));
+  if (P->store != CPM_F64) TRY(pack_factors(P, 0, (cpm_dtype)P->store, P->packed[1], s));
   TRYC(cudaGetLastError());
 #undef TRY
 #undef TRYC
@@ -949,8 +936,6 @@ void oras_destroy(oras_pc* P, cudaStream_t s) {
   dfree(P->col, s);
   dfree(P->dpos, s);
   dfree(P->val, s);
-  dfree(P->val32, s);
-  dfree(P->val16, s);
   dfree(P->lvsub_f, s);
   dfree(P->lvptr_f, s);
   dfree(P->lvrow_f, s);
@@ -960,7 +945,6 @@ void oras_destroy(oras_pc* P, cudaStream_t s) {
   dfree(P->tptr, s);
   dfree(P->tcol, s);
   dfree(P->tval, s);
-  dfree(P->tval32, s);
   dfree(P->tdpos, s);
   dfree(P->lvsub_tf, s);
   dfree(P->lvptr_tf, s);
@@ -972,6 +956,8 @@ void oras_destroy(oras_pc* P, cudaStream_t s) {
   dfree(P->memb, s);
   dfree(P->mloc, s);
   dfree(P->lsub, s);
+  for (auto& pf : P->packed) packed_free(pf, s);
+  dfree(P->err, s);
   delete P;
 }
 

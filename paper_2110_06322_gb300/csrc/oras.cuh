@@ -3,6 +3,24 @@
 
 #include "common.cuh"
 
+// One chunk of level-packed factor rows (see packed.cu): byte offset and size
+// in the packed stream, its rows and entries, and whether its rows divide by
+// a stored diagonal.
+struct ChunkRec {
+  int64_t off;
+  int32_t bytes, nrows, ne, div;
+  int32_t pad[2];
+};
+
+struct PackedFactors {
+  uint8_t* data = nullptr;
+  int64_t bytes = 0;
+  ChunkRec* rec = nullptr;
+  int64_t* chsub = nullptr;  // [np+1] chunk range of each subdomain (forward, then backward)
+  int64_t nchunks = 0;
+  cpm_dtype vtype = CPM_F64;
+};
+
 // Restricted additive Schwarz preconditioner (Section 2.2).  Local rows of all
 // subdomains are numbered globally ("local rows"): subdomain j owns local
 // rows sptr[j] .. sptr[j+1]-1, in its local order.  Column indices in the
@@ -23,9 +41,7 @@ struct oras_pc {
   int64_t* rptr = nullptr;    // [nloc+1] CSR of the local matrices / ILU(0) factors (L\U packed)
   int32_t* col = nullptr;     // [nnz] local column (within the subdomain)
   int32_t* dpos = nullptr;    // [nloc] offset of the diagonal within its row
-  double* val = nullptr;      // [nnz] FP64 factors
-  float* val32 = nullptr;     // [nnz] FP32 factors (store == CPM_F32)
-  __nv_bfloat16* val16 = nullptr;  // [nnz] BF16 factors (store == CPM_BF16)
+  double* val = nullptr;      // [nnz] FP64 factors (CSR; the applies use the packed copies)
   // level schedules: for subdomain j, forward levels lvptr_f[lvsub_f[j] .. lvsub_f[j+1]]
   // index ranges of lvrow_f (local rows, ascending within a level)
   int32_t* lvsub_f = nullptr;  // [np+1]
@@ -39,7 +55,6 @@ struct oras_pc {
   int64_t* tptr = nullptr;
   int32_t* tcol = nullptr;
   double* tval = nullptr;
-  float* tval32 = nullptr;
   int32_t* tdpos = nullptr;
   int32_t* lvsub_tf = nullptr;  // level schedules of the transposed factors
   int64_t* lvptr_tf = nullptr;
@@ -52,6 +67,9 @@ struct oras_pc {
   int32_t* memb = nullptr;    // [nA][KMEM]
   int32_t* mloc = nullptr;    // [nA][KMEM] local row (global numbering)
   int32_t* lsub = nullptr;    // [nloc] subdomain of each local row
+  // level-packed factors: [0] FP64, [1] store type, [2] transposed FP64, [3] transposed FP32
+  PackedFactors packed[4];
+  int* err = nullptr;         // device flag: a bounded wait of the apply ran out
 };
 
 namespace cpm {
@@ -61,6 +79,8 @@ constexpr int KMEM = 16;  // most subdomains one node may belong to
 namespace cpm {
 cpm_status oras_build(const cpm_band* B, const oras_params* prm, double c, cudaStream_t s, oras_pc** out);
 cpm_status oras_run(const oras_pc* P, const void* r, void* z, cpm_dtype dt, int nrhs, int transpose, cudaStream_t s);
+cpm_status pack_factors(oras_pc* P, int transposed, cpm_dtype vt, PackedFactors& out, cudaStream_t s);
+void packed_free(PackedFactors& pf, cudaStream_t s);
 void oras_destroy(oras_pc* P, cudaStream_t s);
 cpm_status solve_run(const cpm_band* B, const oras_pc* P, double c, const double* f, double* u,
                      const cpm_solve_params* prm, cpm_solve_info* info, int transpose, cudaStream_t s);

@@ -419,7 +419,7 @@ cpm_status solve_run(const cpm_band* B, const oras_pc* P, double c, const double
                      const cpm_solve_params* prm, cpm_solve_info* info, int transpose, cudaStream_t s) {
   *info = cpm_solve_info{};
   const int64_t n = B->nA;
-  if (prm->mixed && P && !P->val32 && !P->val16)
+  if (prm->mixed && P && P->store == CPM_F64)
     return fail(CPM_ERR_ARG, "mixed precision needs FP32 or BF16 factors (oras_params.store)");
   Work W;
   cpm_status st = W.alloc(n, prm->restart, prm->mixed != 0, s);
@@ -488,6 +488,11 @@ cpm_status solve_run(const cpm_band* B, const oras_pc* P, double c, const double
     dfree(d, s);
   }
   cudaError_t e = cudaStreamSynchronize(s);
+  if (P && e == cudaSuccess) {
+    int herr = 0;
+    cudaMemcpy(&herr, P->err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (herr && st == CPM_OK) st = fail(CPM_ERR_TIMEOUT, "a bounded wait in the Schwarz apply ran out");
+  }
   W.release(s);
   cudaStreamSynchronize(s);
   info->iters = out.iters;

@@ -17,6 +17,8 @@ analytic surfaces stand in):
                  Y = (x^2 - y^2) z (a degree-3 spherical harmonic, eigenvalue -12)
   * TORUS_H004   torus R = 1, r = 0.4, h = 0.004, c = 10, 20 random Fourier modes
   * TORUS_H002   same torus at h = 0.002 (mixed-precision workload)
+  * TORUS_H0125, TORUS_H025   the same torus at h = 0.0125 / 0.025 with 64 / 16
+                 parts (same rows per subdomain), small cases for profiling
 """
 from __future__ import annotations
 
@@ -70,6 +72,10 @@ WORKLOADS = {
     "torus_h0.004": dict(kind=TORUS, params=surface_params(TORUS, a=1.0, b=0.4), h=0.004, p=3, c=10.0,
                          rhs="modes", seed=2, nparts=512, overlap=2, robin=False, alpha=4.0, alpha_cross=20.0,
                          restart=30, rtol=1e-8),
+    "torus_h0.0125": dict(kind=TORUS, params=surface_params(TORUS, a=1.0, b=0.4), h=0.0125, p=3, c=10.0,
+                          rhs="modes", seed=2, nparts=64, overlap=2, robin=False, restart=30, rtol=1e-8),
+    "torus_h0.025": dict(kind=TORUS, params=surface_params(TORUS, a=1.0, b=0.4), h=0.025, p=3, c=10.0,
+                         rhs="modes", seed=2, nparts=16, overlap=2, robin=False, restart=30, rtol=1e-8),
     "torus_h0.002": dict(kind=TORUS, params=surface_params(TORUS, a=1.0, b=0.4), h=0.002, p=3, c=10.0,
                          rhs="modes", seed=3, nparts=512, overlap=2, robin=False, alpha=4.0, alpha_cross=20.0,
                          restart=30, rtol=1e-8),

@@ -37,6 +37,12 @@ def torus005(cpm, oracle_mod):
 
 
 @pytest.fixture(scope="module")
+def torus005_lu(torus005):
+    """Sparse LU of the oracle's M (library factorisation), shared by the tests."""
+    return sla.splu(torus005[2].to_scipy().tocsc())
+
+
+@pytest.fixture(scope="module")
 def sphere01(cpm, oracle_mod):
     B = cpm.Band(0, SPH, 0.1, 3)
     O = oracle_mod.Band(0, SPH, 0.1, 3)
@@ -86,10 +92,10 @@ def test_schwarz_several_rhs(cpm, oracle_mod, sphere01):
 
 
 @pytest.mark.parametrize("robin", [False, True])
-def test_fp64_solve_matches_direct_solve(cpm, oracle_mod, torus005, robin):
+def test_fp64_solve_matches_direct_solve(cpm, oracle_mod, torus005, torus005_lu, robin):
     B, O, M = torus005
     f = inputs.gaussian_vector(4, B.n_active)
-    xd = sla.spsolve(M.to_scipy().tocsc(), f)
+    xd = torus005_lu.solve(f)
     P = cpm.Schwarz(B, 10.0, 16, 2, robin=robin)
     u, info = cpm.solve(B, _cuda(f), P, rtol=1e-13, maxit=5000)
     assert info["status"] == 0, info
@@ -99,10 +105,10 @@ def test_fp64_solve_matches_direct_solve(cpm, oracle_mod, torus005, robin):
     assert np.linalg.norm(u.cpu().numpy() - xo) <= 1e-10 * np.linalg.norm(xo)
 
 
-def test_mixed_precision_solve_reaches_1e8(cpm, oracle_mod, torus005):
+def test_mixed_precision_solve_reaches_1e8(cpm, oracle_mod, torus005, torus005_lu):
     B, O, M = torus005
     f = inputs.gaussian_vector(7, B.n_active)
-    xd = sla.spsolve(M.to_scipy().tocsc(), f)
+    xd = torus005_lu.solve(f)
     for store in (cpm.CPM_F32, cpm.CPM_BF16):
         P = cpm.Schwarz(B, 10.0, 16, 2, robin=True, store=store)
         u, info = cpm.solve(B, _cuda(f), P, rtol=1e-10, mixed=True, maxit=5000)
@@ -121,10 +127,10 @@ def test_sphere_harmonic_solution(cpm, oracle_mod, sphere01):
     assert np.linalg.norm(u.cpu().numpy() - xd) <= 1e-10 * np.linalg.norm(xd)
 
 
-def test_adjoint_solve(cpm, oracle_mod, torus005):
+def test_adjoint_solve(cpm, oracle_mod, torus005, torus005_lu):
     B, O, M = torus005
     g = inputs.gaussian_vector(8, B.n_active)
-    lam_d = sla.spsolve(M.to_scipy().T.tocsc(), g)
+    lam_d = torus005_lu.solve(g, trans="T")
     for robin in (False, True):
         P = cpm.Schwarz(B, 10.0, 16, 2, robin=robin)
         lam, info = cpm.solve(B, _cuda(g), P, rtol=1e-13, adjoint=True, maxit=5000)
