@@ -113,6 +113,22 @@ class Clocks:
                 "samples": len(self.rows)}
 
 
+# ---------------------------------------------------------------- ranks
+def reduce_over_ranks(ms, iters, device="cpu"):
+    """Whole-job numbers of a replicated run: the slowest rank's time and the
+    band-point iterations summed over all ranks (no data-path collective:
+    this is the only exchange)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms), float(iters)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    it = torch.tensor([float(iters)], dtype=torch.float64, device=device)
+    dist.all_reduce(it)
+    return t.item(), it.item()
+
+
 # ---------------------------------------------------------------- oracle sample (CPU)
 def oracle_step(w, h, nparts):
     """One full pipeline of the FP64 oracle on the sample; returns (seconds,
@@ -234,16 +250,7 @@ def run_gpu(args):
         e1.record(stream)
         barrier()
     launches = cpm.cpm_kernel_launches() - L0
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = t.item()
-        tot = torch.tensor([float(iters)], device="cuda")
-        dist.all_reduce(tot)
-        all_iters = tot.item()
-    else:
-        all_iters = iters
+    ms, all_iters = reduce_over_ranks(e0.elapsed_time(e1), iters, device="cuda")
     value = n * all_iters / (ms / 1000.0)
     solves_per_s = 2 * args.steps * world / (ms / 1000.0)
 
@@ -259,12 +266,8 @@ def run_gpu(args):
         lh_pin.copy_(lam, non_blocking=True)
         e_iters += i1["iters"] + i2["iters"]
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = t.item()
-    e2e_value = n * e_iters * world / e2e_s
+    e2e_s, e_all = reduce_over_ranks(time.perf_counter() - t0, e_iters, device="cuda")
+    e2e_value = n * e_all / e2e_s
 
     # ---- plain FP64 solve of the same system (context: mixed vs FP64)
     B = cpm.Band(kind, prm, h, w["p"])

@@ -156,9 +156,11 @@ def oras_apply(pc, r, z, n_active, transpose=False, stream=None):
     return z
 
 
-def cpm_solve(band, pc, c, f, u, restart=30, maxit=10000, rtol=1e-8, mixed=False, reorth=True, inner_rtol=1e-4,
+def cpm_solve(band, pc, c, f, u, restart=30, maxit=10000, rtol=1e-8, mixed=False, reorth=2, inner_rtol=1e-4,
               adjoint=False, timing=False, stream=None):
-    prm = cpm_solve_params(int(restart), int(maxit), float(rtol), int(bool(mixed)), int(bool(reorth)),
+    """reorth: 0 one Gram-Schmidt pass, 1 a second pass when the first shrank the
+    vector below 1/sqrt(2) of its norm, 2 always two passes (default)."""
+    prm = cpm_solve_params(int(restart), int(maxit), float(rtol), int(bool(mixed)), int(reorth),
                            float(inner_rtol), int(bool(timing)))
     info = cpm_solve_info()
     fn = lib().cpm_solve_adjoint if adjoint else lib().cpm_solve

@@ -170,37 +170,47 @@ __global__ void k_loff_T(ApplyGeom G, const T* __restrict__ x, const int32_t* __
   }
 }
 
-template <typename T, int P>
+// LPN lanes per active node: the node's transpose-map entries (ascending
+// row) are split over its lanes and shuffle-reduced in a fixed tree, so the
+// sum order is fixed and the result deterministic.  FP64 uses few lanes per
+// node (the reduction costs FP64 adds); FP32 uses more lanes for coalescing.
+template <typename T, int LPN>
 __global__ void __launch_bounds__(256) k_ET(ApplyGeom G, Shifts S, const int64_t* __restrict__ tptr,
-                                            const uint32_t* __restrict__ tent, const T* __restrict__ x,
-                                            const T* __restrict__ v, T* __restrict__ y) {
-  const int rhs = blockIdx.y;
+                                            const uint32_t* __restrict__ tent, const T* __restrict__ tw,
+                                            const T* __restrict__ x, const T* __restrict__ v, T* __restrict__ y) {
+  constexpr int NPW = 32 / LPN;  // nodes per warp
+  const int rhs = blockIdx.y, lane = threadIdx.x & 31, sub = lane & (LPN - 1);
   x += (int64_t)rhs * G.nA;
   y += (int64_t)rhs * G.nA;
   v += (int64_t)rhs * G.nR;
   const T diag = (T)(S.c[rhs] + 6.0 * G.coef), coef = (T)G.coef;
-  constexpr int P1 = P + 1;
-  for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < G.nA; m += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  // warp-uniform loop over groups of NPW nodes
+  for (int64_t wb = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * NPW; wb < G.nA; wb += nwarps * NPW) {
+    const int64_t m = wb + lane / LPN;
     T acc = 0;
-    for (int64_t e = tptr[m]; e < tptr[m + 1]; ++e) {
-      uint32_t pk = tent[e];
-      int64_t r = pk >> 6;
-      int pos = pk & 63;
-      int u = pos / (P1 * P1), vv = (pos / P1) % P1, t = pos % P1;
-      T W;
-      if constexpr (sizeof(T) == 8) {
-        const double* w = G.w1d + r * 3 * P1;
-        W = (w[u] * w[P1 + vv]) * w[2 * P1 + t];
-      } else {
-        float l0[P1], l1[P1], l2[P1];
-        lagrange_f32<P>(G.s32[3 * r], l0);
-        lagrange_f32<P>(G.s32[3 * r + 1], l1);
-        lagrange_f32<P>(G.s32[3 * r + 2], l2);
-        W = (l0[u] * l1[vv]) * l2[t];
-      }
-      acc += W * v[r];
+    if (m < G.nA) {
+      const int64_t e1 = tptr[m + 1];
+      for (int64_t e = tptr[m] + sub; e < e1; e += LPN) acc += __ldg(tw + e) * v[__ldg(tent + e) >> 6];
     }
-    y[m] = diag * x[m] - coef * acc;
+#pragma unroll
+    for (int o = LPN / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (sub == 0 && m < G.nA) y[m] = diag * x[m] - coef * acc;
+  }
+}
+
+// tensor weight of every transpose-map entry, in the order (w_u w_v) w_w
+__global__ void k_tweights(int64_t n, int P, const uint32_t* __restrict__ tent, const double* __restrict__ w1d,
+                           double* tw64, float* tw32) {
+  const int P1 = P + 1;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t pk = tent[e];
+    const int64_t r = pk >> 6;
+    const int pos = pk & 63, u = pos / (P1 * P1), vv = (pos / P1) % P1, t = pos % P1;
+    const double* w = w1d + r * 3 * P1;
+    const double W = __dmul_rn(__dmul_rn(w[u], w[P1 + vv]), w[2 * P1 + t]);
+    tw64[e] = W;
+    tw32[e] = (float)W;
   }
 }
 
@@ -280,10 +290,12 @@ cpm_status apply_typed(const cpm_band* B, const double* c, const T* x, T* y, int
       else KL(k_erow_apply<T, 2><<<g1, 256, 0, s>>>(G, xr, w));
       KL(k_stencil<T><<<g2, 256, 0, s>>>(G, S, xr, w, yr));
     } else {
-      dim3 g1(grid_for(B->nR, 256), nr), g2(grid_for(B->nA, 256), nr);
+      dim3 g1(grid_for(B->nR, 256), nr);
       KL(k_loff_T<T><<<g1, 256, 0, s>>>(G, xr, B->rijk, w));
-      if (B->p == 3) KL(k_ET<T, 3><<<g2, 256, 0, s>>>(G, S, B->tptr, B->tent, xr, w, yr));
-      else KL(k_ET<T, 2><<<g2, 256, 0, s>>>(G, S, B->tptr, B->tent, xr, w, yr));
+      const T* tw = sizeof(T) == 8 ? (const T*)B->tw64 : (const T*)B->tw32;
+      constexpr int LPN = sizeof(T) == 8 ? 4 : 16;
+      dim3 g3(grid_for(B->nA * LPN, 256), nr);
+      KL(k_ET<T, LPN><<<g3, 256, 0, s>>>(G, S, B->tptr, B->tent, tw, xr, w, yr));
     }
     cudaError_t e = cudaGetLastError();
     dfree(w, s);
@@ -339,6 +351,9 @@ cpm_status build_transpose_map(cpm_band* B, cudaStream_t s) {
   CPM_CUDA(cudaMemsetAsync(cnt, 0, nA * sizeof(int32_t), s));
   KL(k_tfill<<<grid_for(B->nR, 256), 256, 0, s>>>(G, P, B->tptr, cnt, B->tent));
   KL(k_tsort<<<grid_for(nA, 128), 128, 0, s>>>(nA, B->tptr, B->tent));
+  CPM_TRY(dalloc(&B->tw64, total, s));
+  CPM_TRY(dalloc(&B->tw32, total, s));
+  KL(k_tweights<<<grid_for(total, 256), 256, 0, s>>>(total, P, B->tent, B->w1d, B->tw64, B->tw32));
   CPM_CUDA(cudaGetLastError());
   dfree(cnt, s);
   return CPM_OK;

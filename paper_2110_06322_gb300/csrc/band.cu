@@ -374,6 +374,8 @@ void band_free(cpm_band* B, cudaStream_t s) {
   dfree(B->s32, s);
   dfree(B->tptr, s);
   dfree(B->tent, s);
+  dfree(B->tw64, s);
+  dfree(B->tw32, s);
   if (B->wbuf) cudaFreeAsync(B->wbuf, s);
   B->wbuf = nullptr;
   delete B;

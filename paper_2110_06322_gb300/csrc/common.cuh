@@ -126,6 +126,8 @@ struct cpm_band {
   // (row, cube position) pairs whose cube holds m, ascending row
   int64_t* tptr = nullptr;       // [nA + 1]
   uint32_t* tent = nullptr;      // packed row * 64 + position
+  double* tw64 = nullptr;        // tensor weight of each entry, (w_u w_v) w_w in FP64
+  float* tw32 = nullptr;         // the same rounded to FP32
   // scratch for the operator apply
   void* wbuf = nullptr;          // [nR] E x values (FP64 room)
   size_t wbuf_bytes = 0;

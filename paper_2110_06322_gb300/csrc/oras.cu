@@ -141,14 +141,39 @@ __global__ void __launch_bounds__(ASM_WARPS * 32)
 // ------------------------------------------------------------------ partition
 __global__ void k_seg_box(int64_t nA, const int32_t* __restrict__ ijkA, const int32_t* __restrict__ segof,
                           const int32_t* __restrict__ segnp, int* box, int* cnt) {
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nA; q += (int64_t)gridDim.x * blockDim.x) {
-    int s = segof[q];
-    if (segnp[s] <= 1) continue;
-    for (int d = 0; d < 3; ++d) {
-      atomicMin(&box[6 * s + d], ijkA[3 * q + d]);
-      atomicMax(&box[6 * s + 3 + d], ijkA[3 * q + d]);
+  // grid-stride over whole warps so that every lane takes part in the shuffles
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); q0 < nA; q0 += stride) {
+    const int64_t q = q0 + lane;
+    const bool in = q < nA;
+    const int s = in ? segof[q] : -1;
+    const bool act = in && segnp[s] > 1;
+    int v[6] = {INT_MAX, INT_MAX, INT_MAX, INT_MIN, INT_MIN, INT_MIN};
+    if (act)
+      for (int d = 0; d < 3; ++d) v[d] = v[3 + d] = ijkA[3 * q + d];
+    const int s0 = __shfl_sync(0xffffffffu, s, 0);
+    if (__all_sync(0xffffffffu, s == s0 && act)) {
+      // one segment for the whole warp: reduce, then one lane updates
+      for (int o = 16; o > 0; o >>= 1)
+        for (int d = 0; d < 3; ++d) {
+          v[d] = min(v[d], __shfl_xor_sync(0xffffffffu, v[d], o));
+          v[3 + d] = max(v[3 + d], __shfl_xor_sync(0xffffffffu, v[3 + d], o));
+        }
+      if (lane == 0) {
+        for (int d = 0; d < 3; ++d) {
+          atomicMin(&box[6 * s0 + d], v[d]);
+          atomicMax(&box[6 * s0 + 3 + d], v[3 + d]);
+        }
+        atomicAdd(&cnt[s0], 32);
+      }
+    } else if (act) {
+      for (int d = 0; d < 3; ++d) {
+        atomicMin(&box[6 * s + d], v[d]);
+        atomicMax(&box[6 * s + 3 + d], v[3 + d]);
+      }
+      atomicAdd(&cnt[s], 1);
     }
-    atomicAdd(&cnt[s], 1);
   }
 }
 
@@ -581,17 +606,44 @@ __global__ void k_level_fill(int64_t nloc, const int32_t* __restrict__ lsub, con
 }
 
 // ------------------------------------------------------------------ ILU(0)
-constexpr int ILU_WARPS = 4;
+constexpr int ILU_WARPS = 16;
+constexpr int ILU_PF = 4;  // entries per lane of the next pivot row held in registers
 
+struct PivotRow {
+  double piv;
+  int64_t kd, k1;
+  int32_t c[ILU_PF];
+  double u[ILU_PF];
+};
+
+// strict upper part of pivot row kq (final: computed in an earlier level)
+__device__ __forceinline__ void load_pivot(const int64_t* __restrict__ rptr, const int32_t* __restrict__ col,
+                                           const int32_t* __restrict__ dpos, const double* val, int64_t kq,
+                                           int lane, PivotRow& R) {
+  R.kd = rptr[kq] + dpos[kq];
+  R.k1 = rptr[kq + 1];
+  R.piv = val[R.kd];
+#pragma unroll
+  for (int k = 0; k < ILU_PF; ++k) {
+    const int64_t e = R.kd + 1 + lane + 32 * k;
+    R.c[k] = e < R.k1 ? col[e] : -1;
+    R.u[k] = e < R.k1 ? val[e] : 0.0;
+  }
+}
+
+// One CTA per subdomain, one warp per row of the current level.  Row i is
+// eliminated in shared memory: for each k < i of its pattern (ascending),
+// a_ik /= u_kk, then a_ij -= a_ik u_kj for the j > k of row k's pattern that
+// row i also holds (binary search), all in FP64 with one rounding per
+// operation in this order.
 __global__ void __launch_bounds__(ILU_WARPS * 32)
     k_ilu0(const int64_t* __restrict__ sptr, const int32_t* __restrict__ lvsub, const int64_t* __restrict__ lvptr,
            const int32_t* __restrict__ lvrow, const int64_t* __restrict__ rptr, const int32_t* __restrict__ col,
            const int32_t* __restrict__ dpos, double* val, int* err) {
-  __shared__ int32_t s_col[ILU_WARPS][MAXROW];
-  __shared__ double s_val[ILU_WARPS][MAXROW];
+  extern __shared__ __align__(16) unsigned char ilu_smem[];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int32_t* scol = s_col[wid];
-  double* sval = s_val[wid];
+  double* sval = reinterpret_cast<double*>(ilu_smem) + wid * MAXROW;
+  int32_t* scol = reinterpret_cast<int32_t*>(ilu_smem + ILU_WARPS * MAXROW * sizeof(double)) + wid * MAXROW;
   const int j = blockIdx.x;
   const int64_t base = sptr[j];
   for (int32_t L = lvsub[j]; L < lvsub[j + 1]; ++L) {
@@ -604,20 +656,29 @@ __global__ void __launch_bounds__(ILU_WARPS * 32)
         sval[t] = val[e0 + t];
       }
       __syncwarp();
+      PivotRow cur, nxt;
+      if (d > 0) load_pivot(rptr, col, dpos, val, base + scol[0], lane, cur);
       for (int t = 0; t < d; ++t) {
-        const int64_t kq = base + scol[t];
-        const int64_t k0 = rptr[kq], kd = k0 + dpos[kq], k1 = rptr[kq + 1];
-        const double piv = val[kd];
-        const double l = ddv(sval[t], piv);
-        if (piv == 0.0 && lane == 0) atomicExch(err, CPM_ERR_BREAKDOWN);
+        if (t + 1 < d) load_pivot(rptr, col, dpos, val, base + scol[t + 1], lane, nxt);
+        const double l = ddv(sval[t], cur.piv);
+        if (cur.piv == 0.0 && lane == 0) atomicExch(err, CPM_ERR_BREAKDOWN);
         __syncwarp();
         if (lane == 0) sval[t] = l;
-        for (int64_t e = kd + 1 + lane; e < k1; e += 32) {
+#pragma unroll
+        for (int k = 0; k < ILU_PF; ++k) {
+          const int32_t c = cur.c[k];
+          if (c >= 0) {
+            const int pos = lower_b(scol, n, c);
+            if (pos < n && scol[pos] == c) sval[pos] = dsb(sval[pos], dm(l, cur.u[k]));
+          }
+        }
+        for (int64_t e = cur.kd + 1 + 32 * ILU_PF + lane; e < cur.k1; e += 32) {
           const int32_t c = col[e];
           const int pos = lower_b(scol, n, c);
           if (pos < n && scol[pos] == c) sval[pos] = dsb(sval[pos], dm(l, val[e]));
         }
         __syncwarp();
+        cur = nxt;
       }
       if (lane == 0 && sval[d] == 0.0) atomicExch(err, CPM_ERR_BREAKDOWN);
       for (int t = lane; t < n; t += 32) val[e0 + t] = sval[t];
@@ -909,8 +970,12 @@ cpm_status oras_build(const cpm_band* B, const oras_params* prm, double c, cudaS
   // ---- level schedules and ILU(0)
   TRY(build_schedule(P, P->rptr, P->col, P->dpos, 1, &P->lvsub_f, &P->lvptr_f, &P->lvrow_f, &P->max_levels, s));
   TRY(build_schedule(P, P->rptr, P->col, P->dpos, 0, &P->lvsub_b, &P->lvptr_b, &P->lvrow_b, &P->max_levels, s));
-  KL(k_ilu0<<<np, ILU_WARPS * 32, 0, s>>>(P->sptr, P->lvsub_f, P->lvptr_f, P->lvrow_f, P->rptr, P->col, P->dpos,
-                                        P->val, err));
+  {
+    const int sm = ILU_WARPS * MAXROW * (int)(sizeof(double) + sizeof(int32_t));
+    TRYC(cudaFuncSetAttribute(k_ilu0, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    KL(k_ilu0<<<np, ILU_WARPS * 32, sm, s>>>(P->sptr, P->lvsub_f, P->lvptr_f, P->lvrow_f, P->rptr, P->col, P->dpos,
+                                            P->val, err));
+  }
   TRYC(cudaGetLastError());
   TRYC(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
   TRYC(cudaStreamSynchronize(s));
@@ -918,8 +983,13 @@ cpm_status oras_build(const cpm_band* B, const oras_params* prm, double c, cudaS
   // level-packed factors for the applies: FP64, and the stored precision
   TRY(dalloc(&P->err, 1, s));
   TRYC(cudaMemsetAsync(P->err, 0, sizeof(int), s));
-  TRY(pack_factors(P, 0, CPM_F64, P->packed[0], s));
-  if (P->store != CPM_F64) TRY(pack_factors(P, 0, (cpm_dtype)P->store, P->packed[1], s));
+  {
+    const cpm_dtype vts[2] = {CPM_F64, (cpm_dtype)P->store};
+    PackedFactors tmp[2];
+    TRY(pack_factors(P, 0, vts, tmp, P->store != CPM_F64 ? 2 : 1, s));
+    P->packed[0] = tmp[0];
+    P->packed[1] = tmp[1];
+  }
   TRYC(cudaGetLastError());
 #undef TRY
 #undef TRYC

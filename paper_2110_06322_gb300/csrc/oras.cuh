@@ -17,7 +17,8 @@ struct PackedFactors {
   int64_t bytes = 0;
   ChunkRec* rec = nullptr;
   int64_t* chsub = nullptr;  // [np+1] chunk range of each subdomain (forward, then backward)
-  int64_t nchunks = 0;
+  uint16_t* csz = nullptr;   // [nchunks] chunk sizes in 16-byte units
+  int64_t nchunks = 0, max_chunks = 0;
   cpm_dtype vtype = CPM_F64;
 };
 
@@ -79,7 +80,8 @@ constexpr int KMEM = 16;  // most subdomains one node may belong to
 namespace cpm {
 cpm_status oras_build(const cpm_band* B, const oras_params* prm, double c, cudaStream_t s, oras_pc** out);
 cpm_status oras_run(const oras_pc* P, const void* r, void* z, cpm_dtype dt, int nrhs, int transpose, cudaStream_t s);
-cpm_status pack_factors(oras_pc* P, int transposed, cpm_dtype vt, PackedFactors& out, cudaStream_t s);
+cpm_status pack_factors(oras_pc* P, int transposed, const cpm_dtype* vt, PackedFactors* out, int nout,
+                        cudaStream_t s);
 void packed_free(PackedFactors& pf, cudaStream_t s);
 void oras_destroy(oras_pc* P, cudaStream_t s);
 cpm_status solve_run(const cpm_band* B, const oras_pc* P, double c, const double* f, double* u,

@@ -5,10 +5,14 @@
 // then the backward rows (diagonal first, then the strict upper part) level by
 // level.  Consecutive rows of one level are cut into chunks of at most
 // CHUNK_BYTES; a chunk never spans two levels.  A chunk is
+//     [chunk header: {nrows, ne, divide flag, pad}]
 //     [row headers: {local row, entry offset, entry count, pad} x nrows]
 //     [16-bit local columns x ne, padded to 16 bytes]
 //     [values x ne, padded to 16 bytes]
-// so a whole chunk is one contiguous, 16-byte aligned copy.
+// so a whole chunk is one contiguous, 16-byte aligned copy that describes
+// itself; the chunks of one subdomain are contiguous, and a table of their
+// sizes (in 16-byte units) lets the copying thread walk them without reading
+// global metadata on the critical path.
 //
 // The apply runs one CTA per subdomain: thread 0 streams the chunk sequence
 // (forward then backward) into a ring of NSTAGE shared-memory buffers with
@@ -32,16 +36,15 @@ cpm_status oras_build_transpose(oras_pc* P, cudaStream_t s);
 
 namespace {
 
-constexpr int CHUNK_BYTES = 16384;
-constexpr int NSTAGE = 3;
-constexpr int PK_WARPS = 16;
-constexpr unsigned WAIT_LIMIT = 1u << 26;  // polls of one mbarrier before giving up
+constexpr int CHUNK_BYTES = 24576;
+constexpr int NSTAGE = 2;
+constexpr int PK_WARPS = 24;
+constexpr unsigned WAIT_LIMIT = 1u << 22;  // polls of one mbarrier before giving up (seconds at most)
 
 __host__ __device__ inline int64_t pad16(int64_t b) { return (b + 15) & ~(int64_t)15; }
 
-template <typename V>
-__host__ __device__ inline int64_t chunk_bytes(int64_t nrows, int64_t ne) {
-  return 16 * nrows + pad16(2 * ne) + pad16((int64_t)sizeof(V) * ne);
+__host__ __device__ inline int64_t chunk_bytes(int64_t nrows, int64_t ne, int vsize) {
+  return 16 + 16 * nrows + pad16(2 * ne) + pad16((int64_t)vsize * ne);
 }
 
 // ---------------------------------------------------------------- packing
@@ -63,9 +66,9 @@ __device__ __forceinline__ int64_t row_entries(const SweepSrc& S, int64_t q) {
 
 // pass A: one thread per subdomain walks its schedule and cuts chunks.
 // mode 0: count chunks; mode 1: write chunk records and row placements.
-template <typename V>
-__global__ void k_pack_plan(int np, SweepSrc S, int mode, int32_t* nchunks, const int64_t* __restrict__ chbase,
-                            ChunkRec* rec, int32_t* row_chunk, int32_t* row_slot, int32_t* row_eoff, int kindflag) {
+__global__ void k_pack_plan(int np, SweepSrc S, int vsize, int mode, int32_t* nchunks,
+                            const int64_t* __restrict__ chbase, ChunkRec* rec, int32_t* row_chunk, int32_t* row_slot,
+                            int32_t* row_eoff, int kindflag) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= np) return;
   int64_t c = mode ? chbase[j] : 0;
@@ -75,9 +78,9 @@ __global__ void k_pack_plan(int np, SweepSrc S, int mode, int32_t* nchunks, cons
     for (int64_t idx = S.lvptr[L]; idx < S.lvptr[L + 1]; ++idx) {
       const int64_t q = S.lvrow[idx];
       const int64_t e = row_entries(S, q);
-      if (nrows > 0 && chunk_bytes<V>(nrows + 1, ne + e) > CHUNK_BYTES) {
+      if (nrows > 0 && chunk_bytes(nrows + 1, ne + e, vsize) > CHUNK_BYTES) {
         if (mode) {
-          rec[c].bytes = (int32_t)chunk_bytes<V>(nrows, ne);
+          rec[c].bytes = (int32_t)chunk_bytes(nrows, ne, vsize);
           rec[c].nrows = (int32_t)nrows;
           rec[c].ne = (int32_t)ne;
           rec[c].div = kindflag;
@@ -97,7 +100,7 @@ __global__ void k_pack_plan(int np, SweepSrc S, int mode, int32_t* nchunks, cons
     }
     if (nrows > 0) {
       if (mode) {
-        rec[c].bytes = (int32_t)chunk_bytes<V>(nrows, ne);
+        rec[c].bytes = (int32_t)chunk_bytes(nrows, ne, vsize);
         rec[c].nrows = (int32_t)nrows;
         rec[c].ne = (int32_t)ne;
         rec[c].div = kindflag;
@@ -107,15 +110,6 @@ __global__ void k_pack_plan(int np, SweepSrc S, int mode, int32_t* nchunks, cons
     }
   }
   if (!mode) nchunks[j] = cnt;
-}
-
-__global__ void k_chunk_sizes(int64_t n, const ChunkRec* __restrict__ rec, int64_t* sz) {
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x)
-    sz[c] = rec[c].bytes;
-}
-__global__ void k_chunk_offsets(int64_t n, const int64_t* __restrict__ off, ChunkRec* rec) {
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x)
-    rec[c].off = off[c];
 }
 
 // pass B: one warp per scheduled row writes its header and entries
@@ -130,9 +124,16 @@ __global__ void k_pack_write(int64_t nrow, SweepSrc S, const int64_t* __restrict
     const int64_t q = S.lvrow[idx];
     const ChunkRec R = rec[row_chunk[idx]];
     uint8_t* base = data + R.off;
-    int32_t* hdr = reinterpret_cast<int32_t*>(base) + 4 * row_slot[idx];
-    uint16_t* cols = reinterpret_cast<uint16_t*>(base + 16 * (int64_t)R.nrows);
-    V* vals = reinterpret_cast<V*>(base + 16 * (int64_t)R.nrows + pad16(2 * (int64_t)R.ne));
+    int32_t* hdr = reinterpret_cast<int32_t*>(base + 16) + 4 * row_slot[idx];
+    uint16_t* cols = reinterpret_cast<uint16_t*>(base + 16 + 16 * (int64_t)R.nrows);
+    if (lane == 0 && row_slot[idx] == 0) {
+      int32_t* ch = reinterpret_cast<int32_t*>(base);
+      ch[0] = R.nrows;
+      ch[1] = R.ne;
+      ch[2] = R.div;
+      ch[3] = 0;
+    }
+    V* vals = reinterpret_cast<V*>(base + 16 + 16 * (int64_t)R.nrows + pad16(2 * (int64_t)R.ne));
     const int64_t eo = row_eoff[idx];
     const int64_t r0 = S.rptr[q], d = r0 + S.dpos[q], r1 = S.rptr[q + 1];
     const int64_t e0 = S.lower ? r0 : d + 1, e1 = S.lower ? d : r1;
@@ -165,9 +166,16 @@ __global__ void k_pack_write<__nv_bfloat16>(int64_t nrow, SweepSrc S, const int6
     const int64_t q = S.lvrow[idx];
     const ChunkRec R = rec[row_chunk[idx]];
     uint8_t* base = data + R.off;
-    int32_t* hdr = reinterpret_cast<int32_t*>(base) + 4 * row_slot[idx];
-    uint16_t* cols = reinterpret_cast<uint16_t*>(base + 16 * (int64_t)R.nrows);
-    __nv_bfloat16* vals = reinterpret_cast<__nv_bfloat16*>(base + 16 * (int64_t)R.nrows + pad16(2 * (int64_t)R.ne));
+    int32_t* hdr = reinterpret_cast<int32_t*>(base + 16) + 4 * row_slot[idx];
+    uint16_t* cols = reinterpret_cast<uint16_t*>(base + 16 + 16 * (int64_t)R.nrows);
+    if (lane == 0 && row_slot[idx] == 0) {
+      int32_t* ch = reinterpret_cast<int32_t*>(base);
+      ch[0] = R.nrows;
+      ch[1] = R.ne;
+      ch[2] = R.div;
+      ch[3] = 0;
+    }
+    __nv_bfloat16* vals = reinterpret_cast<__nv_bfloat16*>(base + 16 + 16 * (int64_t)R.nrows + pad16(2 * (int64_t)R.ne));
     const int64_t eo = row_eoff[idx];
     const int64_t r0 = S.rptr[q], d = r0 + S.dpos[q], r1 = S.rptr[q + 1];
     const int64_t e0 = S.lower ? r0 : d + 1, e1 = S.lower ? d : r1;
@@ -189,74 +197,109 @@ __global__ void k_pack_write<__nv_bfloat16>(int64_t nrow, SweepSrc S, const int6
   }
 }
 
-template <typename V>
-cpm_status pack_one(oras_pc* P, const SweepSrc* sw, PackedFactors& out, cudaStream_t s) {
+__global__ void k_chunk_sizes_v(int64_t n, const ChunkRec* __restrict__ plan, int vsize, int64_t* sz) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x)
+    sz[c] = chunk_bytes(plan[c].nrows, plan[c].ne, vsize);
+}
+__global__ void k_chunk_place(int64_t n, const ChunkRec* __restrict__ plan, const int64_t* __restrict__ off,
+                              const int64_t* __restrict__ sz, ChunkRec* rec, uint16_t* csz) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+    ChunkRec R = plan[c];
+    R.off = off[c];
+    R.bytes = (int32_t)sz[c];
+    rec[c] = R;
+    csz[c] = (uint16_t)(sz[c] >> 4);
+  }
+}
+
+// Chunk plan shared by every value type: cut with the FP64 sizes, so the
+// chunks of narrower types fit the budget too.
+struct Plan {
+  int64_t nch = 0, max_chunks = 0;
+  ChunkRec* rec = nullptr;   // nrows, ne, div per chunk
+  int64_t* chsub = nullptr;  // [np+1]
+  int32_t* rc[2] = {nullptr, nullptr};  // per sweep and schedule position: chunk, slot, entry offset
+  int32_t* rs[2] = {nullptr, nullptr};
+  int32_t* re[2] = {nullptr, nullptr};
+  void release(cudaStream_t s) {
+    dfree(rec, s);
+    dfree(chsub, s);
+    for (int w = 0; w < 2; ++w) {
+      dfree(rc[w], s);
+      dfree(rs[w], s);
+      dfree(re[w], s);
+    }
+  }
+};
+
+cpm_status make_plan(oras_pc* P, const SweepSrc* sw, int vsize, Plan& pl, cudaStream_t s) {
   const int np = P->np;
   const int64_t nloc = P->nloc;
   int32_t* cnt = nullptr;
   int64_t* chbase[2] = {nullptr, nullptr};
-  int32_t *rc = nullptr, *rs = nullptr, *re = nullptr;
-  int64_t* sz = nullptr;
-  int64_t* off = nullptr;
   CPM_TRY(dalloc(&cnt, np, s));
-  // chunk counts per subdomain for both sweeps; layout: subdomain j owns the
-  // chunks [chsub[j], chsub[j+1]): its forward chunks, then its backward chunks
   std::vector<int32_t> hc[2];
   for (int w = 0; w < 2; ++w) {
-    KL(k_pack_plan<V><<<(np + 127) / 128, 128, 0, s>>>(np, sw[w], 0, cnt, nullptr, nullptr, nullptr, nullptr,
-                                                       nullptr, sw[w].div));
+    KL(k_pack_plan<<<(np + 127) / 128, 128, 0, s>>>(np, sw[w], vsize, 0, cnt, nullptr, nullptr, nullptr, nullptr,
+                                                    nullptr, sw[w].div));
     hc[w].resize(np);
     CPM_CUDA(cudaMemcpyAsync(hc[w].data(), cnt, np * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   }
   CPM_CUDA(cudaStreamSynchronize(s));
   std::vector<int64_t> chsub(np + 1, 0), hbase[2];
+  pl.max_chunks = 0;
   hbase[0].resize(np);
   hbase[1].resize(np);
   for (int j = 0; j < np; ++j) {
     hbase[0][j] = chsub[j];
     hbase[1][j] = chsub[j] + hc[0][j];
     chsub[j + 1] = chsub[j] + hc[0][j] + hc[1][j];
+    pl.max_chunks = std::max<int64_t>(pl.max_chunks, hc[0][j] + hc[1][j]);
   }
-  const int64_t nch = chsub[np];
-  out.nchunks = nch;
-  CPM_TRY(dalloc(&out.rec, nch, s));
-  CPM_TRY(dalloc(&out.chsub, np + 1, s));
-  CPM_CUDA(cudaMemcpyAsync(out.chsub, chsub.data(), (np + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-  CPM_TRY(dalloc(&rc, nloc, s));
-  CPM_TRY(dalloc(&rs, nloc, s));
-  CPM_TRY(dalloc(&re, nloc, s));
+  pl.nch = chsub[np];
+  CPM_TRY(dalloc(&pl.rec, pl.nch, s));
+  CPM_TRY(dalloc(&pl.chsub, np + 1, s));
+  CPM_CUDA(cudaMemcpyAsync(pl.chsub, chsub.data(), (np + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
   for (int w = 0; w < 2; ++w) {
     CPM_TRY(dalloc(&chbase[w], np, s));
     CPM_CUDA(cudaMemcpyAsync(chbase[w], hbase[w].data(), np * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-  }
-  CPM_TRY(dalloc(&sz, nch, s));
-  CPM_TRY(dalloc(&off, nch + 1, s));
-  // chunk records of both sweeps, then their byte offsets
-  for (int w = 0; w < 2; ++w)
-    KL(k_pack_plan<V><<<(np + 127) / 128, 128, 0, s>>>(np, sw[w], 1, nullptr, chbase[w], out.rec, rc, rs, re,
-                                                       sw[w].div));
-  KL(k_chunk_sizes<<<grid_for(nch, 256), 256, 0, s>>>(nch, out.rec, sz));
-  CPM_TRY(scan_exclusive_i64(sz, off, nch, s));
-  KL(k_chunk_offsets<<<grid_for(nch, 256), 256, 0, s>>>(nch, off, out.rec));
-  CPM_CUDA(cudaMemcpyAsync(&out.bytes, off + nch, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  CPM_CUDA(cudaStreamSynchronize(s));
-  CPM_TRY(dalloc(&out.data, out.bytes, s));
-  for (int w = 0; w < 2; ++w) {
-    // row placements (per schedule position) of sweep w, then its data; the
-    // re-plan rewrites the same records and leaves their offsets in place
-    KL(k_pack_plan<V><<<(np + 127) / 128, 128, 0, s>>>(np, sw[w], 1, nullptr, chbase[w], out.rec, rc, rs, re,
-                                                       sw[w].div));
-    KL(k_pack_write<V><<<grid_for(nloc * 32, 256), 256, 0, s>>>(nloc, sw[w], P->sptr, P->lsub, out.rec, rc, rs, re,
-                                                               out.data));
+    CPM_TRY(dalloc(&pl.rc[w], nloc, s));
+    CPM_TRY(dalloc(&pl.rs[w], nloc, s));
+    CPM_TRY(dalloc(&pl.re[w], nloc, s));
+    KL(k_pack_plan<<<(np + 127) / 128, 128, 0, s>>>(np, sw[w], vsize, 1, nullptr, chbase[w], pl.rec, pl.rc[w],
+                                                    pl.rs[w], pl.re[w], sw[w].div));
   }
   CPM_CUDA(cudaGetLastError());
   CPM_CUDA(cudaStreamSynchronize(s));
   dfree(cnt, s);
   dfree(chbase[0], s);
   dfree(chbase[1], s);
-  dfree(rc, s);
-  dfree(rs, s);
-  dfree(re, s);
+  return CPM_OK;
+}
+
+template <typename V>
+cpm_status emit(oras_pc* P, const SweepSrc* sw, const Plan& pl, PackedFactors& out, cudaStream_t s) {
+  const int np = P->np;
+  const int64_t nch = pl.nch;
+  int64_t *sz = nullptr, *off = nullptr;
+  CPM_TRY(dalloc(&sz, nch, s));
+  CPM_TRY(dalloc(&off, nch + 1, s));
+  CPM_TRY(dalloc(&out.rec, nch, s));
+  CPM_TRY(dalloc(&out.csz, nch, s));
+  out.max_chunks = pl.max_chunks;
+  CPM_TRY(dalloc(&out.chsub, np + 1, s));
+  CPM_CUDA(cudaMemcpyAsync(out.chsub, pl.chsub, (np + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+  KL(k_chunk_sizes_v<<<grid_for(nch, 256), 256, 0, s>>>(nch, pl.rec, (int)sizeof(V), sz));
+  CPM_TRY(scan_exclusive_i64(sz, off, nch, s));
+  KL(k_chunk_place<<<grid_for(nch, 256), 256, 0, s>>>(nch, pl.rec, off, sz, out.rec, out.csz));
+  CPM_CUDA(cudaMemcpyAsync(&out.bytes, off + nch, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  CPM_CUDA(cudaStreamSynchronize(s));
+  out.nchunks = nch;
+  CPM_TRY(dalloc(&out.data, out.bytes, s));
+  for (int w = 0; w < 2; ++w)
+    KL(k_pack_write<V><<<grid_for(P->nloc * 32, 256), 256, 0, s>>>(P->nloc, sw[w], P->sptr, P->lsub, out.rec,
+                                                                  pl.rc[w], pl.rs[w], pl.re[w], out.data));
+  CPM_CUDA(cudaGetLastError());
   dfree(sz, s);
   dfree(off, s);
   return CPM_OK;
@@ -297,6 +340,8 @@ __device__ __forceinline__ T cvt(V v) {
 }
 
 struct PkArgs {
+  const uint16_t* csz;
+  int64_t csz_bytes;  // shared-memory bytes reserved for the chunk-size table
   const int64_t* sptr;
   const int32_t* snode;
   const uint8_t* owned;
@@ -308,91 +353,148 @@ struct PkArgs {
   int* err;
 };
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// barrier among the consumer warps only (named barrier 1)
+__device__ __forceinline__ void consumer_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(PK_WARPS * 32) : "memory");
+}
+
+template <typename T, typename V>
+__device__ __forceinline__ T row_dot(const int4 h, int e0, int lane, const V* vals, const uint16_t* cols,
+                                     const T* xs) {
+  T s = 0;
+  for (int e = e0 + lane; e < h.z; e += 32) s += cvt<V, T>(vals[h.y + e]) * xs[cols[h.y + e]];
+  return s;
+}
+
+// Warps 0..PK_WARPS-1 consume chunks; warp PK_WARPS produces them (one lane
+// issues the bulk copies).  full[s]: a chunk landed in stage s (transaction
+// count); empty[s]: the consumers finished with stage s.
 template <typename T, typename V, bool SMEMX>
-__global__ void __launch_bounds__(PK_WARPS * 32)
+__global__ void __launch_bounds__((PK_WARPS + 1) * 32)
     k_schwarz_pk(PkArgs A, const T* __restrict__ r, T* __restrict__ z, T* xglob) {
   extern __shared__ __align__(128) unsigned char pk_smem[];
-  __shared__ uint64_t full[NSTAGE];
+  __shared__ uint64_t full[NSTAGE], empty[NSTAGE];
   __shared__ int abort_flag;
   const int j = blockIdx.x, rhs = blockIdx.y;
   const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+  const bool producer = wid == PK_WARPS;
   r += (int64_t)rhs * A.nA;
   z += (int64_t)rhs * A.nA;
   unsigned char* ring = pk_smem;
+  uint16_t* csz = reinterpret_cast<uint16_t*>(pk_smem + NSTAGE * CHUNK_BYTES);  // chunk sizes / 16
   const int64_t base = A.sptr[j], n = A.sptr[j + 1] - base;
-  T* xs = SMEMX ? reinterpret_cast<T*>(pk_smem + NSTAGE * CHUNK_BYTES) : xglob + (int64_t)rhs * A.nloc + base;
+  T* xs = SMEMX ? reinterpret_cast<T*>(pk_smem + NSTAGE * CHUNK_BYTES + A.csz_bytes)
+                : xglob + (int64_t)rhs * A.nloc + base;
   const int64_t c0 = A.chsub[j], nch = A.chsub[j + 1] - c0;
+  for (int64_t c = tid; c < nch; c += blockDim.x) csz[c] = A.csz[c0 + c];
   if (tid == 0) {
     abort_flag = 0;
-    for (int q = 0; q < NSTAGE; ++q) mbar_init(&full[q], 1);
+    for (int q = 0; q < NSTAGE; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], 1);
+    }
     fence_mbar_init();
   }
   __syncthreads();
-  if (tid == 0)
-    for (int64_t c = 0; c < nch && c < NSTAGE; ++c) {
-      const ChunkRec R = A.rec[c0 + c];
-      mbar_expect_tx(&full[c], (uint32_t)R.bytes);
-      bulk_g2s(ring + c * CHUNK_BYTES, A.data + R.off, (uint32_t)R.bytes, &full[c]);
+  if (producer) {
+    if (lane == 0) {
+      int64_t off = nch > 0 ? A.rec[c0].off : 0;
+      for (int64_t c = 0; c < nch; ++c) {
+        const int st = (int)(c % NSTAGE);
+        if (c >= NSTAGE) {  // wait until the consumers released this stage
+          unsigned polls = 0;
+          bool ok = true;
+          while (!mbar_try_wait(&empty[st], (uint32_t)(((c / NSTAGE) - 1) & 1)))
+            if (++polls > WAIT_LIMIT) {
+              ok = false;
+              break;
+            }
+          if (!ok || *(volatile int*)&abort_flag) {
+            abort_flag = 1;
+            break;
+          }
+        }
+        const uint32_t bytes = (uint32_t)csz[c] << 4;
+        fence_proxy_async();
+        mbar_expect_tx(&full[st], bytes);
+        bulk_g2s(ring + st * CHUNK_BYTES, A.data + off, bytes, &full[st]);
+        off += bytes;
+      }
     }
-  for (int64_t q = tid; q < n; q += blockDim.x) {
-    const T v = r[A.snode[base + q]];
-    xs[q] = (A.transpose && !A.owned[base + q]) ? (T)0 : v;
+  } else {
+    for (int64_t q = tid; q < n; q += PK_WARPS * 32) {
+      const T v = r[A.snode[base + q]];
+      xs[q] = (A.transpose && !A.owned[base + q]) ? (T)0 : v;
+    }
+    consumer_sync();
+    for (int64_t c = 0; c < nch; ++c) {
+      const int st = (int)(c % NSTAGE);
+      const uint32_t par = (uint32_t)((c / NSTAGE) & 1);
+      unsigned polls = 0;
+      while (!mbar_try_wait(&full[st], par)) {
+        if (++polls > WAIT_LIMIT) {
+          abort_flag = 1;
+          break;
+        }
+      }
+      const unsigned char* buf = ring + st * CHUNK_BYTES;
+      const int4 ch = *reinterpret_cast<const int4*>(buf);  // {nrows, ne, divide, pad}
+      const int4* hdr = reinterpret_cast<const int4*>(buf + 16);
+      const uint16_t* cols = reinterpret_cast<const uint16_t*>(buf + 16 + 16 * (int64_t)ch.x);
+      const V* vals = reinterpret_cast<const V*>(buf + 16 + 16 * (int64_t)ch.x + pad16(2 * (int64_t)ch.y));
+      if (!abort_flag) {
+        const int e0 = ch.z ? 1 : 0;
+        int rr = wid;
+        // two rows at a time: independent accumulations and reductions interleave
+        for (; rr + PK_WARPS < ch.x; rr += 2 * PK_WARPS) {
+          const int4 h0 = hdr[rr], h1 = hdr[rr + PK_WARPS];
+          T s0 = row_dot<T, V>(h0, e0, lane, vals, cols, xs);
+          T s1 = row_dot<T, V>(h1, e0, lane, vals, cols, xs);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+          }
+          if (lane == 0) {
+            T v0 = xs[h0.x] - s0, v1 = xs[h1.x] - s1;
+            if (ch.z) {
+              v0 = v0 / cvt<V, T>(vals[h0.y]);
+              v1 = v1 / cvt<V, T>(vals[h1.y]);
+            }
+            xs[h0.x] = v0;
+            xs[h1.x] = v1;
+          }
+        }
+        if (rr < ch.x) {
+          const int4 h = hdr[rr];
+          T s0 = row_dot<T, V>(h, e0, lane, vals, cols, xs);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+          if (lane == 0) {
+            T v = xs[h.x] - s0;
+            if (ch.z) v = v / cvt<V, T>(vals[h.y]);
+            xs[h.x] = v;
+          }
+        }
+      }
+      consumer_sync();  // level barrier; the stage is free again
+      if (tid == 0) mbar_arrive(&empty[st]);
+      if (abort_flag) break;
+    }
   }
   __syncthreads();
-  int64_t issued = nch < NSTAGE ? nch : NSTAGE;
-  for (int64_t c = 0; c < nch; ++c) {
-    const int st = (int)(c % NSTAGE);
-    const uint32_t par = (uint32_t)((c / NSTAGE) & 1);
-    unsigned polls = 0;
-    while (!mbar_try_wait(&full[st], par)) {
-      if (++polls > WAIT_LIMIT) {
-        abort_flag = 1;
-        break;
-      }
-    }
-    const ChunkRec R = A.rec[c0 + c];
-    const unsigned char* buf = ring + st * CHUNK_BYTES;
-    const int32_t* hdr = reinterpret_cast<const int32_t*>(buf);
-    const uint16_t* cols = reinterpret_cast<const uint16_t*>(buf + 16 * (int64_t)R.nrows);
-    const V* vals = reinterpret_cast<const V*>(buf + 16 * (int64_t)R.nrows + pad16(2 * (int64_t)R.ne));
-    if (!abort_flag) {
-      for (int rr = wid; rr < R.nrows; rr += PK_WARPS) {
-        const int4 h = reinterpret_cast<const int4*>(hdr)[rr];
-        const int q = h.x, eo = h.y, cnt = h.z;
-        const int e0 = R.div ? 1 : 0;
-        T s = 0;
-        for (int e = e0 + lane; e < cnt; e += 32) s += cvt<V, T>(vals[eo + e]) * xs[cols[eo + e]];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) {
-          T v = xs[q] - s;
-          if (R.div) v = v / cvt<V, T>(vals[eo]);
-          xs[q] = v;
-        }
-      }
-    }
-    __syncthreads();
-    if (abort_flag) break;
-    // refill the stage just consumed (only thread 0 issues copies)
-    if (tid == 0 && issued < nch) {
-      const int st2 = (int)(issued % NSTAGE);
-      const ChunkRec R2 = A.rec[c0 + issued];
-      fence_proxy_async();
-      mbar_expect_tx(&full[st2], (uint32_t)R2.bytes);
-      bulk_g2s(ring + st2 * CHUNK_BYTES, A.data + R2.off, (uint32_t)R2.bytes, &full[st2]);
-      ++issued;
-    }
-  }
   if (abort_flag) {
-    if (tid == 0) {
-      atomicExch(A.err, CPM_ERR_TIMEOUT);
-      // drain copies in flight (bounded) before the shared memory goes away
-      for (int64_t c = 0; c < issued; ++c) {
+    if (tid == 0) atomicExch(A.err, CPM_ERR_TIMEOUT);
+    // drain copies in flight (bounded) before the shared memory goes away
+    if (producer && lane == 0)
+      for (int q = 0; q < NSTAGE; ++q) {
         unsigned polls = 0;
-        while (!mbar_try_wait(&full[c % NSTAGE], (uint32_t)((c / NSTAGE) & 1)) && ++polls < WAIT_LIMIT) {
+        while (!mbar_try_wait(&full[q], 0) && !mbar_try_wait(&full[q], 1) && ++polls < WAIT_LIMIT) {
         }
       }
-    }
     return;
   }
   if (!A.transpose) {
@@ -419,11 +521,14 @@ __global__ void k_gather_T2(int64_t nA, int64_t nloc, const int32_t* __restrict_
 
 }  // namespace
 
-// Build the level-packed factors (forward rows, then backward rows) with
-// values of type V from the CSR factors; transposed selects the transposed
-// factors (U^T with its diagonal first, then L^T).
-cpm_status pack_factors(oras_pc* P, int transposed, cpm_dtype vt, PackedFactors& out, cudaStream_t s) {
-  if (P->max_rows > 65535) return fail(CPM_ERR_ARG, "subdomain of %lld rows exceeds 16-bit local columns", (long long)P->max_rows);
+// Build level-packed factors (forward rows, then backward rows) from the CSR
+// factors, one packed stream per requested value type (nout of them, types
+// vt[]); transposed selects the transposed factors (U^T with its diagonal
+// first, then L^T).
+cpm_status pack_factors(oras_pc* P, int transposed, const cpm_dtype* vt, PackedFactors* out, int nout,
+                        cudaStream_t s) {
+  if (P->max_rows > 65535)
+    return fail(CPM_ERR_ARG, "subdomain of %lld rows exceeds 16-bit local columns", (long long)P->max_rows);
   SweepSrc sw[2];
   if (!transposed) {
     sw[0] = {P->rptr, P->col, P->dpos, P->val, P->lvsub_f, P->lvptr_f, P->lvrow_f, 1, 0};
@@ -432,15 +537,28 @@ cpm_status pack_factors(oras_pc* P, int transposed, cpm_dtype vt, PackedFactors&
     sw[0] = {P->tptr, P->tcol, P->tdpos, P->tval, P->lvsub_tf, P->lvptr_tf, P->lvrow_tf, 1, 1};
     sw[1] = {P->tptr, P->tcol, P->tdpos, P->tval, P->lvsub_tb, P->lvptr_tb, P->lvrow_tb, 0, 0};
   }
-  out.vtype = vt;
-  if (vt == CPM_F64) return pack_one<double>(P, sw, out, s);
-  if (vt == CPM_F32) return pack_one<float>(P, sw, out, s);
-  return pack_one<__nv_bfloat16>(P, sw, out, s);
+  cpm_status st = CPM_OK;
+  for (int k = 0; k < nout && st == CPM_OK; ++k) {
+    // chunks are cut per value type so that every type fills the budget
+    const int vsize = vt[k] == CPM_F64 ? 8 : (vt[k] == CPM_F32 ? 4 : 2);
+    Plan pl;
+    st = make_plan(P, sw, vsize, pl, s);
+    out[k].vtype = vt[k];
+    if (st == CPM_OK) {
+      if (vt[k] == CPM_F64) st = emit<double>(P, sw, pl, out[k], s);
+      else if (vt[k] == CPM_F32) st = emit<float>(P, sw, pl, out[k], s);
+      else st = emit<__nv_bfloat16>(P, sw, pl, out[k], s);
+    }
+    cudaStreamSynchronize(s);
+    pl.release(s);
+  }
+  return st;
 }
 
 void packed_free(PackedFactors& pf, cudaStream_t s) {
   dfree(pf.data, s);
   dfree(pf.rec, s);
+  dfree(pf.csz, s);
   dfree(pf.chsub, s);
   pf.nchunks = 0;
   pf.bytes = 0;
@@ -460,7 +578,9 @@ static cpm_status run_pk(const oras_pc* P, const PackedFactors& pf, const T* r, 
   A.nA = P->nA;
   A.nloc = P->nloc;
   A.err = P->err;
-  const size_t ring = (size_t)NSTAGE * CHUNK_BYTES;
+  A.csz = pf.csz;
+  A.csz_bytes = pad16(2 * pf.max_chunks);
+  const size_t ring = (size_t)NSTAGE * CHUNK_BYTES + A.csz_bytes;
   const size_t xsb = (size_t)P->max_rows * sizeof(T);
   const bool smemx = ring + xsb <= 113 * 1024;  // two CTAs per SM
   T* xloc = nullptr;
@@ -472,12 +592,12 @@ static cpm_status run_pk(const oras_pc* P, const PackedFactors& pf, const T* r, 
     if (smemx) {
       const size_t sm = ring + xsb;
       CPM_CUDA(cudaFuncSetAttribute(k_schwarz_pk<T, V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      KL(k_schwarz_pk<T, V, true><<<g, PK_WARPS * 32, sm, s>>>(A, r + (int64_t)r0 * P->nA, z + (int64_t)r0 * P->nA,
+      KL(k_schwarz_pk<T, V, true><<<g, (PK_WARPS + 1) * 32, sm, s>>>(A, r + (int64_t)r0 * P->nA, z + (int64_t)r0 * P->nA,
                                                                xl));
     } else {
       CPM_CUDA(cudaFuncSetAttribute(k_schwarz_pk<T, V, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)ring));
-      KL(k_schwarz_pk<T, V, false><<<g, PK_WARPS * 32, ring, s>>>(A, r + (int64_t)r0 * P->nA,
+      KL(k_schwarz_pk<T, V, false><<<g, (PK_WARPS + 1) * 32, ring, s>>>(A, r + (int64_t)r0 * P->nA,
                                                                   z + (int64_t)r0 * P->nA, xl));
     }
     if (transpose) {
@@ -500,7 +620,7 @@ cpm_status oras_run(const oras_pc* Pc, const void* r, void* z, cpm_dtype dt, int
   PackedFactors& pf = P->packed[slot];
   if (!pf.data) {
     const cpm_dtype vt = dt == CPM_F64 ? CPM_F64 : (transpose ? CPM_F32 : (cpm_dtype)P->store);
-    CPM_TRY(pack_factors(P, transpose, vt, pf, s));
+    CPM_TRY(pack_factors(P, transpose, &vt, &pf, 1, s));
   }
   if (dt == CPM_F64) return run_pk<double, double>(P, pf, (const double*)r, (double*)z, nrhs, transpose, s);
   if (pf.vtype == CPM_BF16)

@@ -21,7 +21,7 @@ namespace cpm {
 namespace {
 
 constexpr int RED_THREADS = 256;
-constexpr int RED_BLOCKS = 152 * 2;
+constexpr int RED_BLOCKS = 152 * 8;
 constexpr int CH = 16;  // basis vectors per Gram-Schmidt pass kernel
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
@@ -51,10 +51,12 @@ __global__ void __launch_bounds__(RED_THREADS)
     for (int t = 0; t < CH; ++t)
       if (t < nv) acc[t] += V[t * ld + i] * wi;
   }
-  for (int t = 0; t < nv; ++t) {
-    const double s = block_sum(acc[t], sh);
-    if (threadIdx.x == 0) partial[t * gridDim.x + blockIdx.x] = s;
-  }
+#pragma unroll
+  for (int t = 0; t < CH; ++t)
+    if (t < nv) {  // nv is uniform over the block
+      const double s = block_sum(acc[t], sh);
+      if (threadIdx.x == 0) partial[t * gridDim.x + blockIdx.x] = s;
+    }
 }
 
 // w -= sum_t coef[t] V_t  (t < nv); when norm != 0 also partial sums of w^2
@@ -80,21 +82,26 @@ __global__ void __launch_bounds__(RED_THREADS)
   }
 }
 
-// out[t] (+)= sum_b partial[t * nb + b], fixed order
+// out[t] (+)= sum_b partial[t * nb + b] in a fixed order; block t reduces value t
 __global__ void k_reduce(const double* __restrict__ partial, int nvals, int nb, double* out, int accumulate) {
   __shared__ double sh[RED_THREADS / 32];
-  for (int t = 0; t < nvals; ++t) {
-    double v = 0;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) v += partial[t * nb + b];
-    const double s = block_sum(v, sh);
-    if (threadIdx.x == 0) out[t] = accumulate ? out[t] + s : s;
-  }
+  const int t = blockIdx.x;
+  double v = 0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) v += partial[t * nb + b];
+  const double s = block_sum(v, sh);
+  if (threadIdx.x == 0) out[t] = accumulate ? out[t] + s : s;
 }
 
-__global__ void k_scale(const double* __restrict__ w, const double* __restrict__ nrm, double* v, int64_t n) {
-  const double inv = 1.0 / sqrt(*nrm);
+// v = w * (*inv)
+__global__ void k_scale(const double* __restrict__ w, const double* __restrict__ inv, double* v, int64_t n) {
+  const double a = *inv;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    v[i] = w[i] * inv;
+    v[i] = w[i] * a;
+}
+
+// out[0] = 1 / sqrt(in[0]) (one thread)
+__global__ void k_rsqrt1(const double* __restrict__ in, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) out[0] = 1.0 / sqrt(in[0]);
 }
 
 __global__ void k_sub(const double* __restrict__ f, double* r, int64_t n) {  // r = f - r
@@ -145,6 +152,7 @@ __global__ void k_givens(double* H, int m, const double* __restrict__ hc, double
   for (int i = 0; i <= j; ++i) H[i * m + j] = col[i];
   pub[0] = fabs(g[j + 1]);
   pub[1] = hn;
+  pub[2] = hn > 0.0 ? 1.0 / hn : 0.0;  // scale of the next basis vector
 }
 
 // y = H(0:k,0:k)^{-1} g (upper triangular), one thread
@@ -176,7 +184,7 @@ struct Work {
   double *V = nullptr, *w = nullptr, *z = nullptr, *t = nullptr, *r = nullptr;
   float *v32 = nullptr, *z32 = nullptr, *w32 = nullptr;
   double *H = nullptr, *hc = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr, *ny = nullptr;
-  double *partial = nullptr, *scal = nullptr;
+  double *partial = nullptr, *scal = nullptr;  // partial: (32 + 1) x RED_BLOCKS
   double* pub = nullptr;  // pinned host
   cpm_status alloc(int64_t n_, int m_, bool f32, cudaStream_t s) {
     n = n_;
@@ -198,7 +206,7 @@ struct Work {
     CPM_TRY(dalloc(&g, m + 1, s));
     CPM_TRY(dalloc(&y, m, s));
     CPM_TRY(dalloc(&ny, m, s));
-    CPM_TRY(dalloc(&partial, (size_t)(CH + 1) * RED_BLOCKS, s));
+    CPM_TRY(dalloc(&partial, (size_t)(32 + 1) * RED_BLOCKS, s));
     CPM_TRY(dalloc(&scal, 8, s));
     CPM_CUDA(cudaMallocHost((void**)&pub, 8 * sizeof(double)));
     return CPM_OK;
@@ -291,29 +299,43 @@ cpm_status norm2(const double* a, int64_t n, double* out, Work& W, cudaStream_t 
   return CPM_OK;
 }
 
-// Gram-Schmidt of w against V_0..V_j; hc[0..j] = coefficients, hc[j+1] = |w|^2
-cpm_status gram_schmidt(int j, int reorth, Work& W, cudaStream_t s) {
+// Classical Gram-Schmidt of w against V_0..V_j; hc[0..j] = coefficients,
+// hc[j+1] = |w|^2 after orthogonalisation.  reorth: 0 one pass; 1 a second
+// pass when the first one shrank |w| below 1/sqrt(2) of its value (the
+// Daniel-Gragg-Kaufman-Stewart criterion); 2 always two passes.
+cpm_status gs_pass(int j, bool first, bool want_norm, Work& W, cudaStream_t s) {
   const int nv = j + 1;
-  for (int pass = 0; pass < (reorth ? 2 : 1); ++pass) {
-    for (int t0 = 0; t0 < nv; t0 += CH) {
-      const int nc = nv - t0 < CH ? nv - t0 : CH;
-      KL(k_dots<<<GB, RED_THREADS, 0, s>>>(W.V + (int64_t)t0 * W.n, W.n, nc, W.w, W.n, W.partial));
-      // pass 0 writes the coefficients; pass 1 adds to them; the update uses
-      // this pass's coefficients (kept in y as scratch)
-      KL(k_reduce<<<1, RED_THREADS, 0, s>>>(W.partial, nc, GB, W.y + t0, 0));
-    }
-    if (pass == 0) CPM_CUDA(cudaMemcpyAsync(W.hc, W.y, nv * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    else KL(k_add<<<1, 256, 0, s>>>(W.hc, W.y, nv));  // second pass: coefficients accumulate
-    const bool last = pass == (reorth ? 1 : 0);
-    for (int t0 = 0; t0 < nv; t0 += CH) {
-      const int nc = nv - t0 < CH ? nv - t0 : CH;
-      const bool lastchunk = last && t0 + CH >= nv;
-      KL(k_update<<<GB, RED_THREADS, 0, s>>>(W.V + (int64_t)t0 * W.n, W.n, nc, W.y + t0, W.w, W.n, lastchunk ? 1 : 0,
-                                          W.partial));
-    }
+  for (int t0 = 0; t0 < nv; t0 += CH) {
+    const int nc = nv - t0 < CH ? nv - t0 : CH;
+    KL(k_dots<<<GB, RED_THREADS, 0, s>>>(W.V + (int64_t)t0 * W.n, W.n, nc, W.w, W.n, W.partial));
+    KL(k_reduce<<<nc, RED_THREADS, 0, s>>>(W.partial, nc, GB, W.y + t0, 0));
   }
-  KL(k_reduce<<<1, RED_THREADS, 0, s>>>(W.partial, 1, GB, W.hc + j + 1, 0));
+  if (first) CPM_CUDA(cudaMemcpyAsync(W.hc, W.y, nv * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  else KL(k_add<<<1, 256, 0, s>>>(W.hc, W.y, nv));
+  for (int t0 = 0; t0 < nv; t0 += CH) {
+    const int nc = nv - t0 < CH ? nv - t0 : CH;
+    const bool lastchunk = want_norm && t0 + CH >= nv;
+    KL(k_update<<<GB, RED_THREADS, 0, s>>>(W.V + (int64_t)t0 * W.n, W.n, nc, W.y + t0, W.w, W.n, lastchunk ? 1 : 0,
+                                           W.partial));
+  }
+  if (want_norm) KL(k_reduce<<<1, RED_THREADS, 0, s>>>(W.partial, 1, GB, W.hc + j + 1, 0));
   CPM_CUDA(cudaGetLastError());
+  return CPM_OK;
+}
+
+cpm_status gram_schmidt(int j, int reorth, Work& W, cudaStream_t s) {
+  if (reorth == 1) {
+    CPM_TRY(norm2(W.w, W.n, W.scal + 6, W, s));
+    CPM_TRY(gs_pass(j, true, true, W, s));
+    double nn[2];
+    CPM_CUDA(cudaMemcpyAsync(&nn[0], W.scal + 6, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CPM_CUDA(cudaMemcpyAsync(&nn[1], W.hc + j + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CPM_CUDA(cudaStreamSynchronize(s));
+    if (nn[1] < 0.5 * nn[0]) CPM_TRY(gs_pass(j, false, true, W, s));
+    return CPM_OK;
+  }
+  CPM_TRY(gs_pass(j, true, reorth == 0, W, s));
+  if (reorth == 2) CPM_TRY(gs_pass(j, false, true, W, s));
   return CPM_OK;
 }
 
@@ -377,7 +399,8 @@ cpm_status gmres(const Ops& o, const double* f, double* x, int m, int maxit, dou
       return CPM_OK;
     }
     out.cycles++;
-    KL(k_scale<<<G, 256, 0, s>>>(W.r, W.scal + 1, W.V, n));
+    KL(k_rsqrt1<<<1, 32, 0, s>>>(W.scal + 1, W.scal + 5));
+    KL(k_scale<<<G, 256, 0, s>>>(W.r, W.scal + 5, W.V, n));
     KL(k_init_g<<<1, 256, 0, s>>>(W.g, m, W.scal + 1));
     int k = 0;
     for (int j = 0; j < m && out.iters < maxit; ++j) {
@@ -386,7 +409,7 @@ cpm_status gmres(const Ops& o, const double* f, double* x, int m, int maxit, dou
       CPM_TRY(op_M(o, W.z, W.w, W, s));
       CPM_TRY(gram_schmidt(j, reorth, W, s));
       KL(k_givens<<<1, 1, 0, s>>>(W.H, m, W.hc, W.cs, W.sn, W.g, j, W.scal + 2));
-      CPM_CUDA(cudaMemcpyAsync(W.pub, W.scal + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CPM_CUDA(cudaMemcpyAsync(W.pub, W.scal + 2, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
       CPM_CUDA(cudaStreamSynchronize(s));
       CPM_CUDA(cudaGetLastError());
       out.iters++;
@@ -397,7 +420,7 @@ cpm_status gmres(const Ops& o, const double* f, double* x, int m, int maxit, dou
         return fail(CPM_ERR_NAN, "Krylov iteration produced NaN or Inf");
       }
       if (hn == 0.0 || est <= rtol * fn) break;
-      if (j + 1 < m) KL(k_scale<<<G, 256, 0, s>>>(W.w, W.hc + j + 1, W.V + (int64_t)(j + 1) * n, n));
+      if (j + 1 < m) KL(k_scale<<<G, 256, 0, s>>>(W.w, W.scal + 4, W.V + (int64_t)(j + 1) * n, n));
     }
     // x += P (V y)
     KL(k_trisolve<<<1, 1, 0, s>>>(W.H, m, W.g, k, W.y));
