@@ -41,6 +41,11 @@ from paper_2110_06322_gb300 import inputs  # noqa: E402
 
 WORKLOAD = "torus_h0.004"
 SAMPLE = dict(h=0.025, nparts=16)  # oracle sample: same torus, same subdomain size
+# DRAM bytes per stored factor entry of one FP32 Schwarz apply (dram__bytes_read.sum + dram__bytes_write.sum
+# of one ncu capture on the torus h = 0.0125 / 64-part case, 564.64 MB over 88,019,898 entries; summary in
+# profiles/k_schwarz_pk_fp32_torus_h0.0125.md).  Traffic grows with the stored entries, so a full launch moves
+# this times Sigma nnz(A_j).  Re-measure when k_schwarz_pk changes.
+SCHWARZ_TRAFFIC_PER_ENTRY = 564.644608e6 / 88019898
 METRIC = "ORAS-GMRES band-pt*iters/s (full pipeline: band, set-up, mixed forward + adjoint solve at 1e-8)"
 UNIT = "band-pt*iters/s"
 
@@ -315,7 +320,8 @@ def run_gpu(args):
         "gpu_launches": launches,
         "roofline": {"kernel": "k_schwarz<float,float> (FP32 Schwarz apply)", "bound": "hbm",
                      "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": None, "alg_bytes_per_launch": alg_bytes, "avg_ms": avg_ms},
+                     "traffic": SCHWARZ_TRAFFIC_PER_ENTRY * nnz, "alg_bytes_per_launch": alg_bytes,
+                     "avg_ms": avg_ms},
         "clocks": clk.summary(),
     }
     if not args.no_cpu_baseline and world == 1:
