@@ -171,8 +171,10 @@ cpm_status oras_export(const oras_pc* pc, int32_t* part, int64_t* sub_ptr, int32
 /* ------------------------------------------------------------------ solver
  * Restarted GMRES(restart), right preconditioned by the Schwarz preconditioner
  * (Section 4.1.1: GMRES is the default Krylov method): classical Gram-Schmidt
- * (reorth 0: one pass; 1: a second pass when the first shrank the vector below
- * 1/sqrt(2) of its norm; 2: always two passes), Givens least squares, stop
+ * (reorth 0: one pass, the refinement-free classical Gram-Schmidt of PETSc's
+ * GMRES, on which the paper's solver is built (Section 1); 1: a second pass when
+ * the first shrank the vector below 1/sqrt(2) of its norm; 2: always two
+ * passes), Givens least squares, stop
  * when |f - M u|_2 <= rtol |f|_2 (true residual, FP64).
  * mixed = 1: FP64 iterative refinement around an inner GMRES whose operator
  * and preconditioner applies run in FP32 (factors stored per oras_params.store);

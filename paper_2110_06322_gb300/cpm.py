@@ -156,10 +156,11 @@ def oras_apply(pc, r, z, n_active, transpose=False, stream=None):
     return z
 
 
-def cpm_solve(band, pc, c, f, u, restart=30, maxit=10000, rtol=1e-8, mixed=False, reorth=2, inner_rtol=1e-4,
+def cpm_solve(band, pc, c, f, u, restart=30, maxit=10000, rtol=1e-8, mixed=False, reorth=0, inner_rtol=1e-4,
               adjoint=False, timing=False, stream=None):
-    """reorth: 0 one Gram-Schmidt pass, 1 a second pass when the first shrank the
-    vector below 1/sqrt(2) of its norm, 2 always two passes (default)."""
+    """reorth: 0 one classical Gram-Schmidt pass (default, the PETSc GMRES
+    default that the paper's solver runs with), 1 a second pass when the first
+    shrank the vector below 1/sqrt(2) of its norm, 2 always two passes."""
     prm = cpm_solve_params(int(restart), int(maxit), float(rtol), int(bool(mixed)), int(reorth),
                            float(inner_rtol), int(bool(timing)))
     info = cpm_solve_info()

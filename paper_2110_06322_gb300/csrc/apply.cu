@@ -241,18 +241,42 @@ __global__ void k_tfill(ApplyGeom G, int P, const int64_t* __restrict__ tptr, in
   }
 }
 
-__global__ void k_tsort(int64_t nA, const int64_t* __restrict__ tptr, uint32_t* tent) {
-  for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < nA; m += (int64_t)gridDim.x * blockDim.x) {
-    int64_t a = tptr[m], b = tptr[m + 1];
-    for (int64_t i = a + 1; i < b; ++i) {  // insertion sort (segments are short)
-      uint32_t key = tent[i];
-      int64_t j = i - 1;
-      while (j >= a && tent[j] > key) {
-        tent[j + 1] = tent[j];
-        --j;
+// Sort each node's (row, cube position) keys ascending.  One warp per node:
+// the keys are distinct, so a key's place is the number of smaller keys in
+// its segment (counted from a shared-memory copy); segments longer than the
+// staging buffer fall back to an insertion sort by one lane.
+constexpr int TSORT_WARPS = 4, TSORT_CAP = 512;
+__global__ void __launch_bounds__(TSORT_WARPS * 32)
+    k_tsort(int64_t nA, const int64_t* __restrict__ tptr, uint32_t* tent) {
+  __shared__ uint32_t sk[TSORT_WARPS][TSORT_CAP];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t* buf = sk[wid];
+  for (int64_t m = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; m < nA;
+       m += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int64_t a = tptr[m];
+    const int n = (int)(tptr[m + 1] - a);
+    if (n <= TSORT_CAP) {
+      for (int i = lane; i < n; i += 32) buf[i] = tent[a + i];
+      __syncwarp();
+      for (int i = lane; i < n; i += 32) {
+        const uint32_t key = buf[i];
+        int r = 0;
+        for (int k = 0; k < n; ++k) r += buf[k] < key ? 1 : 0;
+        tent[a + r] = key;
       }
-      tent[j + 1] = key;
+      __syncwarp();
+    } else if (lane == 0) {
+      for (int64_t i = a + 1; i < a + n; ++i) {
+        const uint32_t key = tent[i];
+        int64_t j = i - 1;
+        while (j >= a && tent[j] > key) {
+          tent[j + 1] = tent[j];
+          --j;
+        }
+        tent[j + 1] = key;
+      }
     }
+    __syncwarp();
   }
 }
 
@@ -350,7 +374,7 @@ cpm_status build_transpose_map(cpm_band* B, cudaStream_t s) {
   CPM_TRY(dalloc(&B->tent, total, s));
   CPM_CUDA(cudaMemsetAsync(cnt, 0, nA * sizeof(int32_t), s));
   KL(k_tfill<<<grid_for(B->nR, 256), 256, 0, s>>>(G, P, B->tptr, cnt, B->tent));
-  KL(k_tsort<<<grid_for(nA, 128), 128, 0, s>>>(nA, B->tptr, B->tent));
+  KL(k_tsort<<<grid_for(nA * 32, TSORT_WARPS * 32), TSORT_WARPS * 32, 0, s>>>(nA, B->tptr, B->tent));
   CPM_TRY(dalloc(&B->tw64, total, s));
   CPM_TRY(dalloc(&B->tw32, total, s));
   KL(k_tweights<<<grid_for(total, 256), 256, 0, s>>>(total, P, B->tent, B->w1d, B->tw64, B->tw32));

@@ -610,7 +610,7 @@ constexpr int ILU_WARPS = 16;
 constexpr int ILU_PF = 4;  // entries per lane of the next pivot row held in registers
 
 struct PivotRow {
-  double piv;
+  double rpiv;  // 1 / u_kk
   int64_t kd, k1;
   int32_t c[ILU_PF];
   double u[ILU_PF];
@@ -618,11 +618,11 @@ struct PivotRow {
 
 // strict upper part of pivot row kq (final: computed in an earlier level)
 __device__ __forceinline__ void load_pivot(const int64_t* __restrict__ rptr, const int32_t* __restrict__ col,
-                                           const int32_t* __restrict__ dpos, const double* val, int64_t kq,
-                                           int lane, PivotRow& R) {
+                                           const int32_t* __restrict__ dpos, const double* val, const double* rinv,
+                                           int64_t kq, int lane, PivotRow& R) {
   R.kd = rptr[kq] + dpos[kq];
   R.k1 = rptr[kq + 1];
-  R.piv = val[R.kd];
+  R.rpiv = rinv[kq];
 #pragma unroll
   for (int k = 0; k < ILU_PF; ++k) {
     const int64_t e = R.kd + 1 + lane + 32 * k;
@@ -633,13 +633,17 @@ __device__ __forceinline__ void load_pivot(const int64_t* __restrict__ rptr, con
 
 // One CTA per subdomain, one warp per row of the current level.  Row i is
 // eliminated in shared memory: for each k < i of its pattern (ascending),
-// a_ik /= u_kk, then a_ij -= a_ik u_kj for the j > k of row k's pattern that
-// row i also holds (binary search), all in FP64 with one rounding per
-// operation in this order.
+// a_ik *= 1 / u_kk, then a_ij -= a_ik u_kj (one fused multiply-add) for the
+// j > k of row k's pattern that row i also holds (binary search), in FP64.
+// A finished row stores the reciprocal of its pivot for the rows below it,
+// so each row costs one division; the factors agree with the division-and-
+// separate-rounding form to a few units in the last place.  FP64 throughput is
+// the bound here: every warp-wide FP64 instruction costs the same whether one
+// lane or 32 use it.
 __global__ void __launch_bounds__(ILU_WARPS * 32)
     k_ilu0(const int64_t* __restrict__ sptr, const int32_t* __restrict__ lvsub, const int64_t* __restrict__ lvptr,
            const int32_t* __restrict__ lvrow, const int64_t* __restrict__ rptr, const int32_t* __restrict__ col,
-           const int32_t* __restrict__ dpos, double* val, int* err) {
+           const int32_t* __restrict__ dpos, double* val, double* rinv, int* err) {
   extern __shared__ __align__(16) unsigned char ilu_smem[];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double* sval = reinterpret_cast<double*>(ilu_smem) + wid * MAXROW;
@@ -657,11 +661,10 @@ __global__ void __launch_bounds__(ILU_WARPS * 32)
       }
       __syncwarp();
       PivotRow cur, nxt;
-      if (d > 0) load_pivot(rptr, col, dpos, val, base + scol[0], lane, cur);
+      if (d > 0) load_pivot(rptr, col, dpos, val, rinv, base + scol[0], lane, cur);
       for (int t = 0; t < d; ++t) {
-        if (t + 1 < d) load_pivot(rptr, col, dpos, val, base + scol[t + 1], lane, nxt);
-        const double l = ddv(sval[t], cur.piv);
-        if (cur.piv == 0.0 && lane == 0) atomicExch(err, CPM_ERR_BREAKDOWN);
+        if (t + 1 < d) load_pivot(rptr, col, dpos, val, rinv, base + scol[t + 1], lane, nxt);
+        const double l = dm(sval[t], cur.rpiv);
         __syncwarp();
         if (lane == 0) sval[t] = l;
 #pragma unroll
@@ -669,18 +672,21 @@ __global__ void __launch_bounds__(ILU_WARPS * 32)
           const int32_t c = cur.c[k];
           if (c >= 0) {
             const int pos = lower_b(scol, n, c);
-            if (pos < n && scol[pos] == c) sval[pos] = dsb(sval[pos], dm(l, cur.u[k]));
+            if (pos < n && scol[pos] == c) sval[pos] = __fma_rn(-l, cur.u[k], sval[pos]);
           }
         }
         for (int64_t e = cur.kd + 1 + 32 * ILU_PF + lane; e < cur.k1; e += 32) {
           const int32_t c = col[e];
           const int pos = lower_b(scol, n, c);
-          if (pos < n && scol[pos] == c) sval[pos] = dsb(sval[pos], dm(l, val[e]));
+          if (pos < n && scol[pos] == c) sval[pos] = __fma_rn(-l, val[e], sval[pos]);
         }
         __syncwarp();
         cur = nxt;
       }
-      if (lane == 0 && sval[d] == 0.0) atomicExch(err, CPM_ERR_BREAKDOWN);
+      if (lane == 0) {
+        if (sval[d] == 0.0) atomicExch(err, CPM_ERR_BREAKDOWN);
+        rinv[q] = ddv(1.0, sval[d]);
+      }
       for (int t = lane; t < n; t += 32) val[e0 + t] = sval[t];
       __syncwarp();
     }
@@ -710,25 +716,54 @@ __global__ void k_tfill_f(int64_t nloc, const int64_t* __restrict__ sptr, const 
     }
   }
 }
-__global__ void k_tsort_f(int64_t nloc, const int64_t* __restrict__ sptr, const int32_t* __restrict__ lsub,
-                          const int64_t* __restrict__ tptr, int32_t* tcol, double* tval, int32_t* tdpos) {
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nloc; q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t a = tptr[q], b = tptr[q + 1];
-    for (int64_t i = a + 1; i < b; ++i) {
-      const int32_t c = tcol[i];
-      const double v = tval[i];
-      int64_t k = i - 1;
-      while (k >= a && tcol[k] > c) {
-        tcol[k + 1] = tcol[k];
-        tval[k + 1] = tval[k];
-        --k;
-      }
-      tcol[k + 1] = c;
-      tval[k + 1] = v;
-    }
+// Sort each transposed row by local column and record its diagonal's place.
+// One warp per row: the columns of a row are distinct, so an entry's place is
+// the number of smaller columns (counted from a shared-memory copy); rows
+// longer than the staging buffer fall back to an insertion sort by one lane.
+constexpr int TSORT_WARPS = 4, TSORT_CAP = 512;
+__global__ void __launch_bounds__(TSORT_WARPS * 32)
+    k_tsort_f(int64_t nloc, const int64_t* __restrict__ sptr, const int32_t* __restrict__ lsub,
+              const int64_t* __restrict__ tptr, int32_t* tcol, double* tval, int32_t* tdpos) {
+  __shared__ int32_t sc[TSORT_WARPS][TSORT_CAP];
+  __shared__ double sv[TSORT_WARPS][TSORT_CAP];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; q < nloc;
+       q += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int64_t a = tptr[q];
+    const int n = (int)(tptr[q + 1] - a);
     const int32_t me = (int32_t)(q - sptr[lsub[q]]);
-    for (int64_t i = a; i < b; ++i)
-      if (tcol[i] == me) tdpos[q] = (int32_t)(i - a);
+    if (n <= TSORT_CAP) {
+      for (int i = lane; i < n; i += 32) {
+        sc[wid][i] = tcol[a + i];
+        sv[wid][i] = tval[a + i];
+      }
+      __syncwarp();
+      for (int i = lane; i < n; i += 32) {
+        const int32_t c = sc[wid][i];
+        int r = 0;
+        for (int k = 0; k < n; ++k) r += sc[wid][k] < c ? 1 : 0;
+        tcol[a + r] = c;
+        tval[a + r] = sv[wid][i];
+        if (c == me) tdpos[q] = r;
+      }
+      __syncwarp();
+    } else if (lane == 0) {
+      for (int64_t i = a + 1; i < a + n; ++i) {
+        const int32_t c = tcol[i];
+        const double v = tval[i];
+        int64_t k = i - 1;
+        while (k >= a && tcol[k] > c) {
+          tcol[k + 1] = tcol[k];
+          tval[k + 1] = tval[k];
+          --k;
+        }
+        tcol[k + 1] = c;
+        tval[k + 1] = v;
+      }
+      for (int64_t i = a; i < a + n; ++i)
+        if (tcol[i] == me) tdpos[q] = (int32_t)(i - a);
+    }
+    __syncwarp();
   }
 }
 
@@ -796,7 +831,8 @@ cpm_status oras_build_transpose(oras_pc* P, cudaStream_t s) {
   CPM_TRY(dalloc(&P->tdpos, nloc, s));
   CPM_CUDA(cudaMemsetAsync(cnt, 0, nloc * sizeof(int32_t), s));
   KL(k_tfill_f<<<G, 256, 0, s>>>(nloc, P->sptr, P->lsub, P->rptr, P->col, P->val, P->tptr, cnt, P->tcol, P->tval));
-  KL(k_tsort_f<<<G, 256, 0, s>>>(nloc, P->sptr, P->lsub, P->tptr, P->tcol, P->tval, P->tdpos));
+  KL(k_tsort_f<<<grid_for(nloc * 32, TSORT_WARPS * 32), TSORT_WARPS * 32, 0, s>>>(nloc, P->sptr, P->lsub,
+                                                                                   P->tptr, P->tcol, P->tval, P->tdpos));
   CPM_CUDA(cudaGetLastError());
   dfree(cnt, s);
   int32_t ml = 0;
@@ -973,8 +1009,11 @@ cpm_status oras_build(const cpm_band* B, const oras_params* prm, double c, cudaS
   {
     const int sm = ILU_WARPS * MAXROW * (int)(sizeof(double) + sizeof(int32_t));
     TRYC(cudaFuncSetAttribute(k_ilu0, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    double* rinv = nullptr;
+    TRY(dalloc(&rinv, std::max<int64_t>(P->nloc, 1), s));
     KL(k_ilu0<<<np, ILU_WARPS * 32, sm, s>>>(P->sptr, P->lvsub_f, P->lvptr_f, P->lvrow_f, P->rptr, P->col, P->dpos,
-                                            P->val, err));
+                                            P->val, rinv, err));
+    dfree(rinv, s);
   }
   TRYC(cudaGetLastError());
   TRYC(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));

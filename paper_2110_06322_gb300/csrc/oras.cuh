@@ -4,8 +4,8 @@
 #include "common.cuh"
 
 // One chunk of level-packed factor rows (see packed.cu): byte offset and size
-// in the packed stream, its rows and entries, and whether its rows divide by
-// a stored diagonal.
+// in the packed stream, its rows and entries, and whether its rows are scaled
+// by a stored reciprocal diagonal.
 struct ChunkRec {
   int64_t off;
   int32_t bytes, nrows, ne, div;
@@ -18,6 +18,7 @@ struct PackedFactors {
   ChunkRec* rec = nullptr;
   int64_t* chsub = nullptr;  // [np+1] chunk range of each subdomain (forward, then backward)
   uint16_t* csz = nullptr;   // [nchunks] chunk sizes in 16-byte units
+  int32_t* order = nullptr;  // [np] subdomains by decreasing chunk count (launch order)
   int64_t nchunks = 0, max_chunks = 0;
   cpm_dtype vtype = CPM_F64;
 };

@@ -2,10 +2,10 @@
 //
 // Set-up repacks the factors of every subdomain in the order the triangular
 // sweeps consume them: the forward rows (strict lower part) level by level,
-// then the backward rows (diagonal first, then the strict upper part) level by
-// level.  Consecutive rows of one level are cut into chunks of at most
+// then the backward rows (reciprocal diagonal first, then the strict upper
+// part) level by level.  Consecutive rows of one level are cut into chunks of at most
 // CHUNK_BYTES; a chunk never spans two levels.  A chunk is
-//     [chunk header: {nrows, ne, divide flag, pad}]
+//     [chunk header: {nrows, ne, scale-by-diagonal flag, pad}]
 //     [row headers: {local row, entry offset, entry count, pad} x nrows]
 //     [16-bit local columns x ne, padded to 16 bytes]
 //     [values x ne, padded to 16 bytes]
@@ -64,16 +64,26 @@ __device__ __forceinline__ int64_t row_entries(const SweepSrc& S, int64_t q) {
   return (S.lower ? d : n - d - 1) + (S.div ? 1 : 0);
 }
 
-// pass A: one thread per subdomain walks its schedule and cuts chunks.
-// mode 0: count chunks; mode 1: write chunk records and row placements.
-__global__ void k_pack_plan(int np, SweepSrc S, int vsize, int mode, int32_t* nchunks,
-                            const int64_t* __restrict__ chbase, ChunkRec* rec, int32_t* row_chunk, int32_t* row_slot,
-                            int32_t* row_eoff, int kindflag) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= np) return;
-  int64_t c = mode ? chbase[j] : 0;
-  int32_t cnt = 0;
-  for (int32_t L = S.lvsub[j]; L < S.lvsub[j + 1]; ++L) {
+// pass A: one thread per level cuts its rows into chunks (a chunk never spans
+// two levels, so levels are independent).
+// mode 0: lcnt[L] = chunks of level L.
+// mode 1: write chunk records and row placements; level L of subdomain j
+//         starts at chunk chbase[j] + lbase[L] - lbase[lvsub[j]].
+__global__ void k_pack_plan(int32_t nl, int np, SweepSrc S, int vsize, int mode, int32_t* lcnt,
+                            const int64_t* __restrict__ lbase, const int64_t* __restrict__ chbase, ChunkRec* rec,
+                            int32_t* row_chunk, int32_t* row_slot, int32_t* row_eoff, int kindflag) {
+  for (int32_t L = blockIdx.x * blockDim.x + threadIdx.x; L < nl; L += gridDim.x * blockDim.x) {
+    int64_t c = 0;
+    if (mode) {
+      int lo = 0, hi = np - 1;  // the subdomain of level L: the last j with lvsub[j] <= L
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (S.lvsub[mid] <= L) lo = mid;
+        else hi = mid - 1;
+      }
+      c = chbase[lo] + (lbase[L] - lbase[S.lvsub[lo]]);
+    }
+    int32_t cnt = 0;
     int64_t nrows = 0, ne = 0;
     for (int64_t idx = S.lvptr[L]; idx < S.lvptr[L + 1]; ++idx) {
       const int64_t q = S.lvrow[idx];
@@ -105,11 +115,17 @@ __global__ void k_pack_plan(int np, SweepSrc S, int vsize, int mode, int32_t* nc
         rec[c].ne = (int32_t)ne;
         rec[c].div = kindflag;
       }
-      ++c;
       ++cnt;
     }
+    if (!mode) lcnt[L] = cnt;
   }
-  if (!mode) nchunks[j] = cnt;
+}
+
+// chunks of subdomain j in one sweep
+__global__ void k_sub_chunks(int np, const int32_t* __restrict__ lvsub, const int64_t* __restrict__ lbase,
+                             int32_t* cnt) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < np) cnt[j] = (int32_t)(lbase[lvsub[j + 1]] - lbase[lvsub[j]]);
 }
 
 // pass B: one warp per scheduled row writes its header and entries
@@ -143,9 +159,9 @@ __global__ void k_pack_write(int64_t nrow, SweepSrc S, const int64_t* __restrict
       hdr[1] = (int32_t)eo;
       hdr[2] = (int32_t)(e1 - e0 + off);
       hdr[3] = 0;
-      if (S.div) {
+      if (S.div) {  // the diagonal is stored as its reciprocal
         cols[eo] = 0;
-        vals[eo] = (V)S.val[d];
+        vals[eo] = (V)(1.0 / S.val[d]);
       }
     }
     for (int64_t e = e0 + lane; e < e1; e += 32) {
@@ -185,9 +201,9 @@ __global__ void k_pack_write<__nv_bfloat16>(int64_t nrow, SweepSrc S, const int6
       hdr[1] = (int32_t)eo;
       hdr[2] = (int32_t)(e1 - e0 + off);
       hdr[3] = 0;
-      if (S.div) {
+      if (S.div) {  // the diagonal is stored as its reciprocal
         cols[eo] = 0;
-        vals[eo] = __float2bfloat16_rn((float)S.val[d]);
+        vals[eo] = __float2bfloat16_rn((float)(1.0 / S.val[d]));
       }
     }
     for (int64_t e = e0 + lane; e < e1; e += 32) {
@@ -202,8 +218,9 @@ __global__ void k_chunk_sizes_v(int64_t n, const ChunkRec* __restrict__ plan, in
     sz[c] = chunk_bytes(plan[c].nrows, plan[c].ne, vsize);
 }
 __global__ void k_chunk_place(int64_t n, const ChunkRec* __restrict__ plan, const int64_t* __restrict__ off,
-                              const int64_t* __restrict__ sz, ChunkRec* rec, uint16_t* csz) {
+                              const int64_t* __restrict__ sz, ChunkRec* rec, uint16_t* csz, int* err) {
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+    if (sz[c] > CHUNK_BYTES) atomicExch(err, 1);  // a single row larger than a stage buffer
     ChunkRec R = plan[c];
     R.off = off[c];
     R.bytes = (int32_t)sz[c];
@@ -236,16 +253,26 @@ cpm_status make_plan(oras_pc* P, const SweepSrc* sw, int vsize, Plan& pl, cudaSt
   const int np = P->np;
   const int64_t nloc = P->nloc;
   int32_t* cnt = nullptr;
+  int32_t* lcnt[2] = {nullptr, nullptr};
+  int64_t* lbase[2] = {nullptr, nullptr};
   int64_t* chbase[2] = {nullptr, nullptr};
+  int32_t nl[2] = {0, 0};
   CPM_TRY(dalloc(&cnt, np, s));
   std::vector<int32_t> hc[2];
   for (int w = 0; w < 2; ++w) {
-    KL(k_pack_plan<<<(np + 127) / 128, 128, 0, s>>>(np, sw[w], vsize, 0, cnt, nullptr, nullptr, nullptr, nullptr,
-                                                    nullptr, sw[w].div));
+    CPM_CUDA(cudaMemcpyAsync(&nl[w], sw[w].lvsub + np, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CPM_CUDA(cudaStreamSynchronize(s));
+    CPM_TRY(dalloc(&lcnt[w], std::max<int32_t>(nl[w], 1), s));
+    CPM_TRY(dalloc(&lbase[w], (int64_t)nl[w] + 1, s));
+    if (nl[w] > 0)
+      KL(k_pack_plan<<<grid_for(nl[w], 128), 128, 0, s>>>(nl[w], np, sw[w], vsize, 0, lcnt[w], nullptr, nullptr,
+                                                          nullptr, nullptr, nullptr, nullptr, sw[w].div));
+    CPM_TRY(scan_exclusive_i32(lcnt[w], lbase[w], nl[w], s));
+    KL(k_sub_chunks<<<(np + 127) / 128, 128, 0, s>>>(np, sw[w].lvsub, lbase[w], cnt));
     hc[w].resize(np);
     CPM_CUDA(cudaMemcpyAsync(hc[w].data(), cnt, np * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CPM_CUDA(cudaStreamSynchronize(s));
   }
-  CPM_CUDA(cudaStreamSynchronize(s));
   std::vector<int64_t> chsub(np + 1, 0), hbase[2];
   pl.max_chunks = 0;
   hbase[0].resize(np);
@@ -257,7 +284,7 @@ cpm_status make_plan(oras_pc* P, const SweepSrc* sw, int vsize, Plan& pl, cudaSt
     pl.max_chunks = std::max<int64_t>(pl.max_chunks, hc[0][j] + hc[1][j]);
   }
   pl.nch = chsub[np];
-  CPM_TRY(dalloc(&pl.rec, pl.nch, s));
+  CPM_TRY(dalloc(&pl.rec, std::max<int64_t>(pl.nch, 1), s));
   CPM_TRY(dalloc(&pl.chsub, np + 1, s));
   CPM_CUDA(cudaMemcpyAsync(pl.chsub, chsub.data(), (np + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
   for (int w = 0; w < 2; ++w) {
@@ -266,14 +293,18 @@ cpm_status make_plan(oras_pc* P, const SweepSrc* sw, int vsize, Plan& pl, cudaSt
     CPM_TRY(dalloc(&pl.rc[w], nloc, s));
     CPM_TRY(dalloc(&pl.rs[w], nloc, s));
     CPM_TRY(dalloc(&pl.re[w], nloc, s));
-    KL(k_pack_plan<<<(np + 127) / 128, 128, 0, s>>>(np, sw[w], vsize, 1, nullptr, chbase[w], pl.rec, pl.rc[w],
-                                                    pl.rs[w], pl.re[w], sw[w].div));
+    if (nl[w] > 0)
+      KL(k_pack_plan<<<grid_for(nl[w], 128), 128, 0, s>>>(nl[w], np, sw[w], vsize, 1, nullptr, lbase[w], chbase[w],
+                                                          pl.rec, pl.rc[w], pl.rs[w], pl.re[w], sw[w].div));
   }
   CPM_CUDA(cudaGetLastError());
   CPM_CUDA(cudaStreamSynchronize(s));
   dfree(cnt, s);
-  dfree(chbase[0], s);
-  dfree(chbase[1], s);
+  for (int w = 0; w < 2; ++w) {
+    dfree(lcnt[w], s);
+    dfree(lbase[w], s);
+    dfree(chbase[w], s);
+  }
   return CPM_OK;
 }
 
@@ -289,11 +320,31 @@ cpm_status emit(oras_pc* P, const SweepSrc* sw, const Plan& pl, PackedFactors& o
   out.max_chunks = pl.max_chunks;
   CPM_TRY(dalloc(&out.chsub, np + 1, s));
   CPM_CUDA(cudaMemcpyAsync(out.chsub, pl.chsub, (np + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+  {
+    // launch order: longest subdomains first, so the last wave holds the short ones
+    std::vector<int64_t> hs(np + 1);
+    CPM_CUDA(cudaMemcpyAsync(hs.data(), pl.chsub, (np + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CPM_CUDA(cudaStreamSynchronize(s));
+    std::vector<int32_t> ord(np);
+    for (int q = 0; q < np; ++q) ord[q] = q;
+    std::stable_sort(ord.begin(), ord.end(),
+                     [&](int32_t a, int32_t b) { return hs[a + 1] - hs[a] > hs[b + 1] - hs[b]; });
+    CPM_TRY(dalloc(&out.order, np, s));
+    CPM_CUDA(cudaMemcpyAsync(out.order, ord.data(), np * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    CPM_CUDA(cudaStreamSynchronize(s));
+  }
   KL(k_chunk_sizes_v<<<grid_for(nch, 256), 256, 0, s>>>(nch, pl.rec, (int)sizeof(V), sz));
   CPM_TRY(scan_exclusive_i64(sz, off, nch, s));
-  KL(k_chunk_place<<<grid_for(nch, 256), 256, 0, s>>>(nch, pl.rec, off, sz, out.rec, out.csz));
+  int* err = nullptr;
+  CPM_TRY(dalloc(&err, 1, s));
+  CPM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+  KL(k_chunk_place<<<grid_for(nch, 256), 256, 0, s>>>(nch, pl.rec, off, sz, out.rec, out.csz, err));
+  int herr = 0;
   CPM_CUDA(cudaMemcpyAsync(&out.bytes, off + nch, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  CPM_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
   CPM_CUDA(cudaStreamSynchronize(s));
+  dfree(err, s);
+  if (herr) return fail(CPM_ERR_ARG, "a factor row does not fit one %d-byte chunk", CHUNK_BYTES);
   out.nchunks = nch;
   CPM_TRY(dalloc(&out.data, out.bytes, s));
   for (int w = 0; w < 2; ++w)
@@ -340,6 +391,7 @@ __device__ __forceinline__ T cvt(V v) {
 }
 
 struct PkArgs {
+  const int32_t* order;  // subdomains by decreasing chunk count (longest first)
   const uint16_t* csz;
   int64_t csz_bytes;  // shared-memory bytes reserved for the chunk-size table
   const int64_t* sptr;
@@ -378,7 +430,7 @@ __global__ void __launch_bounds__((PK_WARPS + 1) * 32)
   extern __shared__ __align__(128) unsigned char pk_smem[];
   __shared__ uint64_t full[NSTAGE], empty[NSTAGE];
   __shared__ int abort_flag;
-  const int j = blockIdx.x, rhs = blockIdx.y;
+  const int j = A.order[blockIdx.x], rhs = blockIdx.y;
   const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
   const bool producer = wid == PK_WARPS;
   r += (int64_t)rhs * A.nA;
@@ -441,7 +493,7 @@ __global__ void __launch_bounds__((PK_WARPS + 1) * 32)
         }
       }
       const unsigned char* buf = ring + st * CHUNK_BYTES;
-      const int4 ch = *reinterpret_cast<const int4*>(buf);  // {nrows, ne, divide, pad}
+      const int4 ch = *reinterpret_cast<const int4*>(buf);  // {nrows, ne, scale-by-diagonal flag, pad}
       const int4* hdr = reinterpret_cast<const int4*>(buf + 16);
       const uint16_t* cols = reinterpret_cast<const uint16_t*>(buf + 16 + 16 * (int64_t)ch.x);
       const V* vals = reinterpret_cast<const V*>(buf + 16 + 16 * (int64_t)ch.x + pad16(2 * (int64_t)ch.y));
@@ -461,8 +513,8 @@ __global__ void __launch_bounds__((PK_WARPS + 1) * 32)
           if (lane == 0) {
             T v0 = xs[h0.x] - s0, v1 = xs[h1.x] - s1;
             if (ch.z) {
-              v0 = v0 / cvt<V, T>(vals[h0.y]);
-              v1 = v1 / cvt<V, T>(vals[h1.y]);
+              v0 = v0 * cvt<V, T>(vals[h0.y]);
+              v1 = v1 * cvt<V, T>(vals[h1.y]);
             }
             xs[h0.x] = v0;
             xs[h1.x] = v1;
@@ -475,7 +527,7 @@ __global__ void __launch_bounds__((PK_WARPS + 1) * 32)
           for (int o = 16; o > 0; o >>= 1) s0 += __shfl_xor_sync(0xffffffffu, s0, o);
           if (lane == 0) {
             T v = xs[h.x] - s0;
-            if (ch.z) v = v / cvt<V, T>(vals[h.y]);
+            if (ch.z) v = v * cvt<V, T>(vals[h.y]);
             xs[h.x] = v;
           }
         }
@@ -557,6 +609,7 @@ cpm_status pack_factors(oras_pc* P, int transposed, const cpm_dtype* vt, PackedF
 
 void packed_free(PackedFactors& pf, cudaStream_t s) {
   dfree(pf.data, s);
+  dfree(pf.order, s);
   dfree(pf.rec, s);
   dfree(pf.csz, s);
   dfree(pf.chsub, s);
@@ -578,6 +631,7 @@ static cpm_status run_pk(const oras_pc* P, const PackedFactors& pf, const T* r, 
   A.nA = P->nA;
   A.nloc = P->nloc;
   A.err = P->err;
+  A.order = pf.order;
   A.csz = pf.csz;
   A.csz_bytes = pad16(2 * pf.max_chunks);
   const size_t ring = (size_t)NSTAGE * CHUNK_BYTES + A.csz_bytes;

@@ -22,7 +22,6 @@ namespace {
 
 constexpr int RED_THREADS = 256;
 constexpr int RED_BLOCKS = 152 * 8;
-constexpr int CH = 16;  // basis vectors per Gram-Schmidt pass kernel
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -37,49 +36,133 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return t;
 }
 
-// partial[t * gridDim.x + b] = block b's share of <V_t, w>, t < nv
+// partial[b] = block b's share of <a, b>
 __global__ void __launch_bounds__(RED_THREADS)
-    k_dots(const double* __restrict__ V, int64_t ld, int nv, const double* __restrict__ w, int64_t n,
-           double* partial) {
+    k_dot(const double* __restrict__ a, const double* __restrict__ b, int64_t n, double* partial) {
   __shared__ double sh[RED_THREADS / 32];
-  double acc[CH];
-#pragma unroll
-  for (int t = 0; t < CH; ++t) acc[t] = 0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double wi = w[i];
-#pragma unroll
-    for (int t = 0; t < CH; ++t)
-      if (t < nv) acc[t] += V[t * ld + i] * wi;
-  }
-#pragma unroll
-  for (int t = 0; t < CH; ++t)
-    if (t < nv) {  // nv is uniform over the block
-      const double s = block_sum(acc[t], sh);
-      if (threadIdx.x == 0) partial[t * gridDim.x + blockIdx.x] = s;
-    }
+  double acc = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc += a[i] * b[i];
+  const double s = block_sum(acc, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
-// w -= sum_t coef[t] V_t  (t < nv); when norm != 0 also partial sums of w^2
+// Sum NV per-lane values over a warp with NV - 1 + log2(32 / NV) shuffles
+// instead of 5 NV: at each halving step a lane keeps one half of its values
+// and receives its partner's copy of the same half.  On return lane l (and,
+// for NV < 32, every lane congruent to l modulo NV) holds in a[0] the warp
+// sum of value l % NV.
+template <int NV>
+__device__ __forceinline__ void warp_transpose_sum(double (&a)[NV], int lane) {
+#pragma unroll
+  for (int half = NV / 2; half >= 1; half >>= 1) {
+    const bool up = (lane & half) != 0;
+#pragma unroll
+    for (int k = 0; k < half; ++k) {
+      const double send = up ? a[k] : a[k + half];
+      const double keep = up ? a[k + half] : a[k];
+      a[k] = keep + __shfl_xor_sync(0xffffffffu, send, half);
+    }
+  }
+#pragma unroll
+  for (int o = NV; o < 32; o <<= 1) a[0] += __shfl_xor_sync(0xffffffffu, a[0], o);
+}
+
+// Block partial sums of NV per-thread values: partial[t * gridDim.x + b] for
+// t < nv, summed over the block's warps in a fixed order.
+template <int NV>
+__device__ __forceinline__ void block_partials(double (&a)[NV], int nv, double* partial) {
+  __shared__ double sh[RED_THREADS / 32][NV];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  warp_transpose_sum<NV>(a, lane);
+  if (lane < NV) sh[wid][lane] = a[0];
+  __syncthreads();
+  if (threadIdx.x < nv) {
+    double t = 0;
+#pragma unroll
+    for (int q = 0; q < RED_THREADS / 32; ++q) t += sh[q][threadIdx.x];
+    partial[threadIdx.x * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+// Gram-Schmidt pass kernels over nv <= NV basis vectors V_t = V + t ld.
+//   MODE 0: dots     partial <- <V_t, w>
+//   MODE 1: update   w -= sum_t coef[t] V_t
+//   MODE 2: update, then dots of the V_t with the updated w (the second
+//           classical pass's projection fused with the first one's
+//           subtraction: each V_t is read once for both)
+//   MODE 3: update, then partial <- |w|^2
+template <int NV, int MODE>
 __global__ void __launch_bounds__(RED_THREADS)
-    k_update(const double* __restrict__ V, int64_t ld, int nv, const double* __restrict__ coef, double* w, int64_t n,
-             int norm, double* partial) {
-  __shared__ double sh[RED_THREADS / 32];
-  double cf[CH];
+    k_gs(const double* __restrict__ V, int64_t ld, int nv, const double* __restrict__ coef, double* w, int64_t n,
+         double* partial) {
+  __shared__ double cf[NV];
+  if (MODE != 0) {
+    if (threadIdx.x < NV) cf[threadIdx.x] = threadIdx.x < nv ? coef[threadIdx.x] : 0.0;
+    __syncthreads();
+  }
+  constexpr int NA = MODE == 3 ? 1 : NV;
+  double acc[NA];
 #pragma unroll
-  for (int t = 0; t < CH; ++t) cf[t] = t < nv ? coef[t] : 0.0;
-  double acc = 0;
+  for (int t = 0; t < NA; ++t) acc[t] = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double wi = w[i];
+    double v[NV];
 #pragma unroll
-    for (int t = 0; t < CH; ++t)
-      if (t < nv) wi -= cf[t] * V[t * ld + i];
-    w[i] = wi;
-    acc += wi * wi;
+    for (int t = 0; t < NV; ++t) v[t] = t < nv ? V[t * ld + i] : 0.0;
+    double wi = w[i];
+    if (MODE != 0) {
+#pragma unroll
+      for (int t = 0; t < NV; ++t)
+        if (t < nv) wi -= cf[t] * v[t];
+      w[i] = wi;
+    }
+    if (MODE == 0 || MODE == 2) {
+#pragma unroll
+      for (int t = 0; t < NA; ++t)
+        if (t < nv) acc[t] += v[t] * wi;
+    }
+    if (MODE == 3) acc[0] += wi * wi;
   }
-  if (norm) {
-    const double s = block_sum(acc, sh);
-    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+  if constexpr (MODE == 0 || MODE == 2) block_partials<NA>(acc, nv, partial);
+  if constexpr (MODE == 3) block_partials<1>(acc, 1, partial);
+}
+
+// Blocks of one Gram-Schmidt pass kernel: the SM count times the blocks that
+// fit on one SM, fixed per device so that the summation order (and thus the
+// result) does not change between calls.
+template <int NV, int MODE>
+int gs_blocks() {
+  static int cache[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!cache[dev]) {
+    int sms = 0, per = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_gs<NV, MODE>, RED_THREADS, 0);
+    int b = sms * (per > 0 ? per : 1);
+    cache[dev] = b < 1 ? 1 : (b > RED_BLOCKS ? RED_BLOCKS : b);
   }
+  return cache[dev];
+}
+
+// Launch k_gs for nv vectors with the smallest of 8, 16, 32 that holds them;
+// returns the grid used (the number of partial sums per value).
+template <int MODE>
+int launch_gs(const double* V, int64_t ld, int nv, const double* coef, double* w, int64_t n, double* partial,
+              cudaStream_t s) {
+  int g = 0;
+  if (nv <= 8) {
+    g = gs_blocks<8, MODE>();
+    KL(k_gs<8, MODE><<<g, RED_THREADS, 0, s>>>(V, ld, nv, coef, w, n, partial));
+  } else if (nv <= 16) {
+    g = gs_blocks<16, MODE>();
+    KL(k_gs<16, MODE><<<g, RED_THREADS, 0, s>>>(V, ld, nv, coef, w, n, partial));
+  } else {
+    g = gs_blocks<32, MODE>();
+    KL(k_gs<32, MODE><<<g, RED_THREADS, 0, s>>>(V, ld, nv, coef, w, n, partial));
+  }
+  return g;
 }
 
 // out[t] (+)= sum_b partial[t * nb + b] in a fixed order; block t reduces value t
@@ -90,6 +173,20 @@ __global__ void k_reduce(const double* __restrict__ partial, int nvals, int nb, 
   for (int b = threadIdx.x; b < nb; b += blockDim.x) v += partial[t * nb + b];
   const double s = block_sum(v, sh);
   if (threadIdx.x == 0) out[t] = accumulate ? out[t] + s : s;
+}
+
+// y[t] = sum_b partial[t * nb + b] in a fixed order; hc[t] = y[t] (acc 0)
+// or hc[t] += y[t] (acc 1).  Block t reduces value t.
+__global__ void k_reduce_gs(const double* __restrict__ partial, int nb, double* y, double* hc, int acc) {
+  __shared__ double sh[RED_THREADS / 32];
+  const int t = blockIdx.x;
+  double v = 0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) v += partial[t * nb + b];
+  const double s = block_sum(v, sh);
+  if (threadIdx.x == 0) {
+    y[t] = s;
+    hc[t] = acc ? hc[t] + s : s;
+  }
 }
 
 // v = w * (*inv)
@@ -167,10 +264,6 @@ __global__ void k_trisolve(const double* __restrict__ H, int m, const double* __
 
 __global__ void k_negate(const double* __restrict__ a, double* b, int n) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) b[i] = -a[i];
-}
-
-__global__ void k_add(double* a, const double* __restrict__ b, int n) {
-  for (int i = threadIdx.x; i < n; i += blockDim.x) a[i] += b[i];
 }
 
 __global__ void k_init_g(double* g, int m, const double* __restrict__ nrm2) {
@@ -292,9 +385,27 @@ cpm_status op_P(const Ops& o, const double* v, double* out, Work& W, cudaStream_
   return CPM_OK;
 }
 
+// w = M P v.  In FP32 the preconditioned vector stays FP32 between the two
+// applies (its FP64 copy would round back to the same FP32 values).
+cpm_status op_MP(const Ops& o, const double* v, double* w, Work& W, cudaStream_t s) {
+  if (!o.f32 || !o.P) {
+    CPM_TRY(op_P(o, v, W.z, W, s));
+    return op_M(o, W.z, w, W, s);
+  }
+  KL(k_d2f<<<grid_for(W.n, 256), 256, 0, s>>>(v, W.v32, W.n));
+  o.tm->start(s);
+  CPM_TRY(oras_run(o.P, W.v32, W.z32, CPM_F32, 1, o.transpose, s));
+  o.tm->stop(s, true);
+  o.tm->start(s);
+  CPM_TRY(apply_op(o.B, &o.c, W.z32, W.w32, CPM_F32, 1, o.transpose, s));
+  o.tm->stop(s, false);
+  KL(k_f2d<<<grid_for(W.n, 256), 256, 0, s>>>(W.w32, w, W.n));
+  return CPM_OK;
+}
+
 // out[0] = <a, a>
 cpm_status norm2(const double* a, int64_t n, double* out, Work& W, cudaStream_t s) {
-  KL(k_dots<<<GB, RED_THREADS, 0, s>>>(a, 0, 1, a, n, W.partial));
+  KL(k_dot<<<GB, RED_THREADS, 0, s>>>(a, a, n, W.partial));
   KL(k_reduce<<<1, RED_THREADS, 0, s>>>(W.partial, 1, GB, out, 0));
   return CPM_OK;
 }
@@ -303,39 +414,67 @@ cpm_status norm2(const double* a, int64_t n, double* out, Work& W, cudaStream_t 
 // hc[j+1] = |w|^2 after orthogonalisation.  reorth: 0 one pass; 1 a second
 // pass when the first one shrank |w| below 1/sqrt(2) of its value (the
 // Daniel-Gragg-Kaufman-Stewart criterion); 2 always two passes.
-cpm_status gs_pass(int j, bool first, bool want_norm, Work& W, cudaStream_t s) {
-  const int nv = j + 1;
-  for (int t0 = 0; t0 < nv; t0 += CH) {
-    const int nc = nv - t0 < CH ? nv - t0 : CH;
-    KL(k_dots<<<GB, RED_THREADS, 0, s>>>(W.V + (int64_t)t0 * W.n, W.n, nc, W.w, W.n, W.partial));
-    KL(k_reduce<<<nc, RED_THREADS, 0, s>>>(W.partial, nc, GB, W.y + t0, 0));
+//
+// One pass is h = V^T w (kernel MODE 0), then w -= V h (MODE 1 or 3).  With
+// two passes the first pass's subtraction and the second pass's projection
+// run as one kernel (MODE 2), so V is streamed three times instead of four.
+// Bases wider than GS_MAX vectors are processed in chunks of GS_MAX.
+constexpr int GS_MAX = 32;
+
+// dots of w with V_0..V_{nv-1}: y = V^T w and hc = y (acc 0) or hc += y (acc 1)
+cpm_status gs_dots(int nv, bool acc, Work& W, cudaStream_t s) {
+  for (int t0 = 0; t0 < nv; t0 += GS_MAX) {
+    const int nc = nv - t0 < GS_MAX ? nv - t0 : GS_MAX;
+    const int g = launch_gs<0>(W.V + (int64_t)t0 * W.n, W.n, nc, nullptr, W.w, W.n, W.partial, s);
+    KL(k_reduce_gs<<<nc, RED_THREADS, 0, s>>>(W.partial, g, W.y + t0, W.hc + t0, acc ? 1 : 0));
   }
-  if (first) CPM_CUDA(cudaMemcpyAsync(W.hc, W.y, nv * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  else KL(k_add<<<1, 256, 0, s>>>(W.hc, W.y, nv));
-  for (int t0 = 0; t0 < nv; t0 += CH) {
-    const int nc = nv - t0 < CH ? nv - t0 : CH;
-    const bool lastchunk = want_norm && t0 + CH >= nv;
-    KL(k_update<<<GB, RED_THREADS, 0, s>>>(W.V + (int64_t)t0 * W.n, W.n, nc, W.y + t0, W.w, W.n, lastchunk ? 1 : 0,
-                                           W.partial));
+  return CPM_OK;
+}
+
+// w -= V y over V_0..V_{nv-1}; hc[nv] = |w|^2 afterwards
+cpm_status gs_subtract_norm(int nv, Work& W, cudaStream_t s) {
+  int g = 0;
+  for (int t0 = 0; t0 < nv; t0 += GS_MAX) {
+    const int nc = nv - t0 < GS_MAX ? nv - t0 : GS_MAX;
+    const double* Vt = W.V + (int64_t)t0 * W.n;
+    if (t0 + GS_MAX >= nv) g = launch_gs<3>(Vt, W.n, nc, W.y + t0, W.w, W.n, W.partial, s);
+    else launch_gs<1>(Vt, W.n, nc, W.y + t0, W.w, W.n, W.partial, s);
   }
-  if (want_norm) KL(k_reduce<<<1, RED_THREADS, 0, s>>>(W.partial, 1, GB, W.hc + j + 1, 0));
-  CPM_CUDA(cudaGetLastError());
+  KL(k_reduce<<<1, RED_THREADS, 0, s>>>(W.partial, 1, g, W.hc + nv, 0));
   return CPM_OK;
 }
 
 cpm_status gram_schmidt(int j, int reorth, Work& W, cudaStream_t s) {
+  const int nv = j + 1;
   if (reorth == 1) {
     CPM_TRY(norm2(W.w, W.n, W.scal + 6, W, s));
-    CPM_TRY(gs_pass(j, true, true, W, s));
+    CPM_TRY(gs_dots(nv, false, W, s));
+    CPM_TRY(gs_subtract_norm(nv, W, s));
     double nn[2];
     CPM_CUDA(cudaMemcpyAsync(&nn[0], W.scal + 6, sizeof(double), cudaMemcpyDeviceToHost, s));
     CPM_CUDA(cudaMemcpyAsync(&nn[1], W.hc + j + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
     CPM_CUDA(cudaStreamSynchronize(s));
-    if (nn[1] < 0.5 * nn[0]) CPM_TRY(gs_pass(j, false, true, W, s));
+    if (nn[1] < 0.5 * nn[0]) {
+      CPM_TRY(gs_dots(nv, true, W, s));
+      CPM_TRY(gs_subtract_norm(nv, W, s));
+    }
     return CPM_OK;
   }
-  CPM_TRY(gs_pass(j, true, reorth == 0, W, s));
-  if (reorth == 2) CPM_TRY(gs_pass(j, false, true, W, s));
+  CPM_TRY(gs_dots(nv, false, W, s));
+  if (reorth == 2) {
+    if (nv <= GS_MAX) {  // fused: w -= V h1 and h2 = V^T w in one sweep
+      const int g = launch_gs<2>(W.V, W.n, nv, W.y, W.w, W.n, W.partial, s);
+      KL(k_reduce_gs<<<nv, RED_THREADS, 0, s>>>(W.partial, g, W.y, W.hc, 1));
+    } else {
+      for (int t0 = 0; t0 < nv; t0 += GS_MAX) {
+        const int nc = nv - t0 < GS_MAX ? nv - t0 : GS_MAX;
+        launch_gs<1>(W.V + (int64_t)t0 * W.n, W.n, nc, W.y + t0, W.w, W.n, W.partial, s);
+      }
+      CPM_TRY(gs_dots(nv, true, W, s));
+    }
+  }
+  CPM_TRY(gs_subtract_norm(nv, W, s));
+  CPM_CUDA(cudaGetLastError());
   return CPM_OK;
 }
 
@@ -405,8 +544,7 @@ cpm_status gmres(const Ops& o, const double* f, double* x, int m, int maxit, dou
     int k = 0;
     for (int j = 0; j < m && out.iters < maxit; ++j) {
       double* vj = W.V + (int64_t)j * n;
-      CPM_TRY(op_P(o, vj, W.z, W, s));
-      CPM_TRY(op_M(o, W.z, W.w, W, s));
+      CPM_TRY(op_MP(o, vj, W.w, W, s));
       CPM_TRY(gram_schmidt(j, reorth, W, s));
       KL(k_givens<<<1, 1, 0, s>>>(W.H, m, W.hc, W.cs, W.sn, W.g, j, W.scal + 2));
       CPM_CUDA(cudaMemcpyAsync(W.pub, W.scal + 2, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -426,9 +564,9 @@ cpm_status gmres(const Ops& o, const double* f, double* x, int m, int maxit, dou
     KL(k_trisolve<<<1, 1, 0, s>>>(W.H, m, W.g, k, W.y));
     CPM_CUDA(cudaMemsetAsync(W.t, 0, n * sizeof(double), s));
     KL(k_negate<<<1, 256, 0, s>>>(W.y, W.ny, k));
-    for (int t0 = 0; t0 < k; t0 += CH) {
-      const int nc = k - t0 < CH ? k - t0 : CH;
-      KL(k_update<<<GB, RED_THREADS, 0, s>>>(W.V + (int64_t)t0 * n, n, nc, W.ny + t0, W.t, n, 0, nullptr));
+    for (int t0 = 0; t0 < k; t0 += GS_MAX) {
+      const int nc = k - t0 < GS_MAX ? k - t0 : GS_MAX;
+      launch_gs<1>(W.V + (int64_t)t0 * n, n, nc, W.ny + t0, W.t, n, nullptr, s);
     }
     CPM_TRY(op_P(o, W.t, W.z, W, s));
     KL(k_axpy<<<G, 256, 0, s>>>(W.z, x, n));

@@ -3,6 +3,11 @@ forward and adjoint solves) on a named workload, for profiling with ncu:
 no clock sampler, no host oracle, nothing else on the GPU.
 
     python -m paper_2110_06322_gb300.profile_step --workload torus_h0.025 --warmup 3 --steps 1
+
+With --setup-only a step is the set-up alone: band build, Schwarz set-up, and
+one transposed operator and preconditioner apply (which build the transpose
+map and the transposed factors on first use), each phase timed with CUDA
+events.
 """
 from __future__ import annotations
 
@@ -18,6 +23,7 @@ def main():
     ap.add_argument("--workload", default="torus_h0.025")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--setup-only", action="store_true")
     a = ap.parse_args()
     w = inputs.WORKLOADS[a.workload]
     L0 = cpm.cpm_kernel_launches()
@@ -28,7 +34,26 @@ def main():
     del B0
     torch.cuda.synchronize()
     print(f"setup launches={cpm.cpm_kernel_launches() - L0}", flush=True)
-    kw = dict(restart=w["restart"], rtol=w["rtol"], maxit=50000, mixed=True, inner_rtol=1e-4)
+    kw = dict(restart=w["restart"], rtol=w["rtol"], maxit=50000, mixed=True, inner_rtol=1e-4, reorth=0)
+    if a.setup_only:
+        for q in range(a.warmup + a.steps):
+            L0 = cpm.cpm_kernel_launches()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+            ev[0].record()
+            B = cpm.Band(w["kind"], w["params"], w["h"], w["p"])
+            ev[1].record()
+            P = cpm.Schwarz(B, w["c"], w["nparts"], w["overlap"], robin=w["robin"], store=cpm.CPM_F32)
+            ev[2].record()
+            B.apply(w["c"], f.float(), transpose=True)
+            ev[3].record()
+            P.apply(f.float(), transpose=True)
+            ev[4].record()
+            torch.cuda.synchronize()
+            ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(4)]
+            print(f"setup step {q}: band {ms[0]:.1f} ms, schwarz {ms[1]:.1f} ms, first M^T apply {ms[2]:.1f} ms, "
+                  f"first P^T apply {ms[3]:.1f} ms, launches={cpm.cpm_kernel_launches() - L0}", flush=True)
+            del P, B
+        return
     for q in range(a.warmup + a.steps):
         L0 = cpm.cpm_kernel_launches()
         B = cpm.Band(w["kind"], w["params"], w["h"], w["p"])

@@ -105,6 +105,35 @@ def test_fp64_solve_matches_direct_solve(cpm, oracle_mod, torus005, torus005_lu,
     assert np.linalg.norm(u.cpu().numpy() - xo) <= 1e-10 * np.linalg.norm(xo)
 
 
+@pytest.mark.parametrize("reorth", [0, 1, 2])
+def test_gram_schmidt_variants_reach_same_solution(cpm, oracle_mod, torus005, torus005_lu, reorth):
+    """One classical pass, a conditional second pass and two passes: the same
+    solution to 1e-10 (FP64, rtol 1e-12) and to 1e-8 in mixed precision."""
+    B, O, M = torus005
+    f = inputs.gaussian_vector(11, B.n_active)
+    xd = torus005_lu.solve(f)
+    P = cpm.Schwarz(B, 10.0, 16, 2, store=cpm.CPM_F32)
+    u, info = cpm.solve(B, _cuda(f), P, rtol=1e-12, maxit=5000, reorth=reorth)
+    assert info["status"] == 0, info
+    assert np.linalg.norm(u.cpu().numpy() - xd) <= 1e-10 * np.linalg.norm(xd)
+    u, info = cpm.solve(B, _cuda(f), P, rtol=1e-10, maxit=5000, reorth=reorth, mixed=True)
+    assert info["status"] == 0, info
+    assert np.linalg.norm(u.cpu().numpy() - xd) <= 1e-8 * np.linalg.norm(xd)
+
+
+def test_wide_basis_chunked_gram_schmidt(cpm, oracle_mod, sphere01):
+    """Restart 40 without a preconditioner (full cycles of 40 iterations, a
+    basis wider than one Gram-Schmidt kernel's 32 vectors): the chunked passes
+    reach the direct solution."""
+    B, O, M = sphere01
+    f = inputs.gaussian_vector(12, B.n_active)
+    xd = sla.spsolve(M.to_scipy().tocsc(), f)
+    for reorth in (0, 2):
+        u, info = cpm.solve(B, _cuda(f), None, c=1.0, rtol=1e-12, restart=40, maxit=20000, reorth=reorth)
+        assert info["status"] == 0 and info["iters"] > 40, info
+        assert np.linalg.norm(u.cpu().numpy() - xd) <= 1e-10 * np.linalg.norm(xd)
+
+
 def test_mixed_precision_solve_reaches_1e8(cpm, oracle_mod, torus005, torus005_lu):
     B, O, M = torus005
     f = inputs.gaussian_vector(7, B.n_active)
