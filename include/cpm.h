@@ -22,6 +22,12 @@
  *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Every call
  *     is ordered on it.  Only cpm_band_build, oras_setup and cpm_solve* wait
  *     on the host (to size allocations and to fill the info struct).
+ *   - Working memory comes stream-ordered from the device's default memory
+ *     pool (cudaMallocAsync).  On its first allocation on a device the library
+ *     raises that pool's release threshold to 64 GiB, so that memory freed by
+ *     one solve or set-up is reused by the next instead of being returned to
+ *     the driver at every synchronisation; cudaMemPoolTrimTo on the default
+ *     pool gives it back.
  *   - Errors are returned as cpm_status codes; a message for the last error
  *     of the calling thread is available from cpm_last_error().  No call
  *     aborts the process or traps the device.  Kernels that wait on a

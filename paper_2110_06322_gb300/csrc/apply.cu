@@ -174,7 +174,12 @@ __global__ void k_loff_T(ApplyGeom G, const T* __restrict__ x, const int32_t* __
 // row) are split over its lanes and shuffle-reduced in a fixed tree, so the
 // sum order is fixed and the result deterministic.  FP64 uses few lanes per
 // node (the reduction costs FP64 adds); FP32 uses more lanes for coalescing.
-template <typename T, int LPN>
+// Each lane issues the loads of U entries before it uses any of them (the
+// row index, then the gather of v through it), so U chains are in flight;
+// entries past the node's end read row 0 with weight 0, which leaves the sum
+// unchanged.
+constexpr int ET_UNROLL = 4;
+template <typename T, int LPN, int U>
 __global__ void __launch_bounds__(256) k_ET(ApplyGeom G, Shifts S, const int64_t* __restrict__ tptr,
                                             const uint32_t* __restrict__ tent, const T* __restrict__ tw,
                                             const T* __restrict__ x, const T* __restrict__ v, T* __restrict__ y) {
@@ -191,7 +196,20 @@ __global__ void __launch_bounds__(256) k_ET(ApplyGeom G, Shifts S, const int64_t
     T acc = 0;
     if (m < G.nA) {
       const int64_t e1 = tptr[m + 1];
-      for (int64_t e = tptr[m] + sub; e < e1; e += LPN) acc += __ldg(tw + e) * v[__ldg(tent + e) >> 6];
+      for (int64_t e = tptr[m] + sub; e < e1; e += LPN * U) {
+        uint32_t k[U];
+        T w[U], vv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int64_t ee = e + u * LPN;
+          k[u] = ee < e1 ? __ldg(tent + ee) : 0u;
+          w[u] = ee < e1 ? __ldg(tw + ee) : (T)0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) vv[u] = v[k[u] >> 6];
+#pragma unroll
+        for (int u = 0; u < U; ++u) acc += w[u] * vv[u];
+      }
     }
 #pragma unroll
     for (int o = LPN / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -319,7 +337,7 @@ cpm_status apply_typed(const cpm_band* B, const double* c, const T* x, T* y, int
       const T* tw = sizeof(T) == 8 ? (const T*)B->tw64 : (const T*)B->tw32;
       constexpr int LPN = sizeof(T) == 8 ? 4 : 16;
       dim3 g3(grid_for(B->nA * LPN, 256), nr);
-      KL(k_ET<T, LPN><<<g3, 256, 0, s>>>(G, S, B->tptr, B->tent, tw, xr, w, yr));
+      KL(k_ET<T, LPN, ET_UNROLL><<<g3, 256, 0, s>>>(G, S, B->tptr, B->tent, tw, xr, w, yr));
     }
     cudaError_t e = cudaGetLastError();
     dfree(w, s);

@@ -27,6 +27,23 @@ cpm_status fail(cpm_status st, const char* fmt, ...) {
   return st;
 }
 
+void keep_pool_memory() {
+  static std::atomic<unsigned long long> done{0};  // one bit per device (devices 0..63)
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return;
+  }
+  const unsigned long long bit = 1ull << dev;
+  if (done.load() & bit) return;
+  cudaMemPool_t pool;
+  uint64_t thr = 64ull << 30;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess ||
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr) != cudaSuccess)
+    cudaGetLastError();  // not fatal: allocations still work, only slower
+  done.fetch_or(bit);
+}
+
 cpm_status cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
   snprintf(g_err, sizeof(g_err), "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
   return e == cudaErrorMemoryAllocation ? CPM_ERR_OOM : CPM_ERR_CUDA;

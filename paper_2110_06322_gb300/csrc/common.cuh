@@ -37,11 +37,16 @@ cpm_status cuda_fail(cudaError_t e, const char* what, const char* file, int line
     if (s_ != CPM_OK) return s_;         \
   } while (0)
 
+// Raise the release threshold of the current device's default memory pool
+// (once per device), so freed working memory stays in the pool for reuse.
+void keep_pool_memory();
+
 // Device allocation that reports CPM_ERR_OOM.  Stream-ordered.
 template <typename T>
 cpm_status dalloc(T** p, size_t n, cudaStream_t s) {
   *p = nullptr;
   if (n == 0) n = 1;
+  keep_pool_memory();
   cudaError_t e = cudaMallocAsync((void**)p, n * sizeof(T), s);
   if (e == cudaErrorMemoryAllocation) {
     cudaGetLastError();

@@ -17,8 +17,9 @@
 // The apply runs one CTA per subdomain: thread 0 streams the chunk sequence
 // (forward then backward) into a ring of NSTAGE shared-memory buffers with
 // cp.async.bulk (the 1-D TMA copy) and mbarrier transaction counts, NSTAGE-1
-// chunks ahead; all warps consume the current chunk from shared memory (one
-// warp per row: gather the local vector, multiply, shuffle-reduce) and meet at
+// chunks ahead; all warps consume the current chunk from shared memory
+// (SW_LPR lanes per row: gather the local vector, multiply, shuffle-reduce;
+// 32 / SW_LPR rows share each shuffle) and meet at
 // one CTA barrier per chunk, which is also the level barrier.  The local
 // vector lives in shared memory when it fits, else in a global slice.  Every
 // mbarrier wait is bounded; a wait that runs out sets an error flag, the CTA
@@ -413,19 +414,28 @@ __device__ __forceinline__ void consumer_sync() {
   asm volatile("bar.sync 1, %0;" ::"n"(PK_WARPS * 32) : "memory");
 }
 
-template <typename T, typename V>
-__device__ __forceinline__ T row_dot(const int4 h, int e0, int lane, const V* vals, const uint16_t* cols,
+// partial dot product of one packed row with the local vector: lane `sub`
+// of the row's LPR lanes takes entries e0 + sub, e0 + sub + LPR, ...
+template <typename T, typename V, int LPR>
+__device__ __forceinline__ T row_dot(const int4 h, int e0, int sub, const V* vals, const uint16_t* cols,
                                      const T* xs) {
   T s = 0;
-  for (int e = e0 + lane; e < h.z; e += 32) s += cvt<V, T>(vals[h.y + e]) * xs[cols[h.y + e]];
+#pragma unroll 4
+  for (int e = e0 + sub; e < h.z; e += LPR) s += cvt<V, T>(vals[h.y + e]) * xs[cols[h.y + e]];
   return s;
 }
+
+// lanes per factor row in the Schwarz sweeps: 32 / LPR rows share each
+// shuffle of the row reductions.  Rows hold ~60 entries; 8 lanes per row
+// measured best for FP32 and FP64 on the 512-part torus (16 and 32 lanes
+// spend more issue slots and FP64 adds on the reductions).
+constexpr int SW_LPR = 8;
 
 // Warps 0..PK_WARPS-1 consume chunks; warp PK_WARPS produces them (one lane
 // issues the bulk copies).  full[s]: a chunk landed in stage s (transaction
 // count); empty[s]: the consumers finished with stage s.
 template <typename T, typename V, bool SMEMX>
-__global__ void __launch_bounds__((PK_WARPS + 1) * 32)
+__global__ void __launch_bounds__((PK_WARPS + 1) * 32, 2)
     k_schwarz_pk(PkArgs A, const T* __restrict__ r, T* __restrict__ z, T* xglob) {
   extern __shared__ __align__(128) unsigned char pk_smem[];
   __shared__ uint64_t full[NSTAGE], empty[NSTAGE];
@@ -498,35 +508,23 @@ __global__ void __launch_bounds__((PK_WARPS + 1) * 32)
       const uint16_t* cols = reinterpret_cast<const uint16_t*>(buf + 16 + 16 * (int64_t)ch.x);
       const V* vals = reinterpret_cast<const V*>(buf + 16 + 16 * (int64_t)ch.x + pad16(2 * (int64_t)ch.y));
       if (!abort_flag) {
-        const int e0 = ch.z ? 1 : 0;
-        int rr = wid;
-        // two rows at a time: independent accumulations and reductions interleave
-        for (; rr + PK_WARPS < ch.x; rr += 2 * PK_WARPS) {
-          const int4 h0 = hdr[rr], h1 = hdr[rr + PK_WARPS];
-          T s0 = row_dot<T, V>(h0, e0, lane, vals, cols, xs);
-          T s1 = row_dot<T, V>(h1, e0, lane, vals, cols, xs);
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        constexpr int LPR = SW_LPR, RPW = 32 / LPR;  // lanes per row, rows per warp
+        const int e0 = ch.z ? 1 : 0, sub = lane & (LPR - 1);
+        // rows rb + RPW * wid + lane / LPR; the loop is warp-uniform so that
+        // every lane reaches the shuffles
+        for (int rb = 0; rb < ch.x; rb += RPW * PK_WARPS) {
+          const int rr = rb + RPW * wid + lane / LPR;
+          const bool has = rr < ch.x;
+          int4 h = make_int4(0, 0, 0, 0);
+          T sdot = 0;
+          if (has) {
+            h = hdr[rr];
+            sdot = row_dot<T, V, LPR>(h, e0, sub, vals, cols, xs);
           }
-          if (lane == 0) {
-            T v0 = xs[h0.x] - s0, v1 = xs[h1.x] - s1;
-            if (ch.z) {
-              v0 = v0 * cvt<V, T>(vals[h0.y]);
-              v1 = v1 * cvt<V, T>(vals[h1.y]);
-            }
-            xs[h0.x] = v0;
-            xs[h1.x] = v1;
-          }
-        }
-        if (rr < ch.x) {
-          const int4 h = hdr[rr];
-          T s0 = row_dot<T, V>(h, e0, lane, vals, cols, xs);
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-          if (lane == 0) {
-            T v = xs[h.x] - s0;
+          for (int o = LPR / 2; o > 0; o >>= 1) sdot += __shfl_xor_sync(0xffffffffu, sdot, o);
+          if (has && sub == 0) {
+            T v = xs[h.x] - sdot;
             if (ch.z) v = v * cvt<V, T>(vals[h.y]);
             xs[h.x] = v;
           }
