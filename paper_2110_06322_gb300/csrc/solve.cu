@@ -146,7 +146,7 @@ int gs_blocks() {
   return cache[dev];
 }
 
-// Launch k_gs for nv vectors with the smallest of 8, 16, 32 that holds them;
+// Launch k_gs for nv <= 16 vectors with the smaller of 8, 16 that holds them;
 // returns the grid used (the number of partial sums per value).
 template <int MODE>
 int launch_gs(const double* V, int64_t ld, int nv, const double* coef, double* w, int64_t n, double* partial,
@@ -155,12 +155,9 @@ int launch_gs(const double* V, int64_t ld, int nv, const double* coef, double* w
   if (nv <= 8) {
     g = gs_blocks<8, MODE>();
     KL(k_gs<8, MODE><<<g, RED_THREADS, 0, s>>>(V, ld, nv, coef, w, n, partial));
-  } else if (nv <= 16) {
+  } else {
     g = gs_blocks<16, MODE>();
     KL(k_gs<16, MODE><<<g, RED_THREADS, 0, s>>>(V, ld, nv, coef, w, n, partial));
-  } else {
-    g = gs_blocks<32, MODE>();
-    KL(k_gs<32, MODE><<<g, RED_THREADS, 0, s>>>(V, ld, nv, coef, w, n, partial));
   }
   return g;
 }
@@ -418,13 +415,21 @@ cpm_status norm2(const double* a, int64_t n, double* out, Work& W, cudaStream_t 
 // One pass is h = V^T w (kernel MODE 0), then w -= V h (MODE 1 or 3).  With
 // two passes the first pass's subtraction and the second pass's projection
 // run as one kernel (MODE 2), so V is streamed three times instead of four.
-// Bases wider than GS_MAX vectors are processed in chunks of GS_MAX.
-constexpr int GS_MAX = 32;
+// Bases wider than GS_MAX vectors are processed in chunks of at most GS_MAX
+// (balanced: 20 vectors run as 10 + 10): the 16-vector kernels keep enough
+// warps per SM to stream V at close to full bandwidth, where a 32-vector
+// kernel's register use leaves one block per SM.
+constexpr int GS_MAX = 16;
+inline int gs_chunk(int nv) {
+  const int nch = (nv + GS_MAX - 1) / GS_MAX;
+  return (nv + nch - 1) / nch;
+}
 
 // dots of w with V_0..V_{nv-1}: y = V^T w and hc = y (acc 0) or hc += y (acc 1)
 cpm_status gs_dots(int nv, bool acc, Work& W, cudaStream_t s) {
-  for (int t0 = 0; t0 < nv; t0 += GS_MAX) {
-    const int nc = nv - t0 < GS_MAX ? nv - t0 : GS_MAX;
+  const int cs = gs_chunk(nv);
+  for (int t0 = 0; t0 < nv; t0 += cs) {
+    const int nc = nv - t0 < cs ? nv - t0 : cs;
     const int g = launch_gs<0>(W.V + (int64_t)t0 * W.n, W.n, nc, nullptr, W.w, W.n, W.partial, s);
     KL(k_reduce_gs<<<nc, RED_THREADS, 0, s>>>(W.partial, g, W.y + t0, W.hc + t0, acc ? 1 : 0));
   }
@@ -434,10 +439,11 @@ cpm_status gs_dots(int nv, bool acc, Work& W, cudaStream_t s) {
 // w -= V y over V_0..V_{nv-1}; hc[nv] = |w|^2 afterwards
 cpm_status gs_subtract_norm(int nv, Work& W, cudaStream_t s) {
   int g = 0;
-  for (int t0 = 0; t0 < nv; t0 += GS_MAX) {
-    const int nc = nv - t0 < GS_MAX ? nv - t0 : GS_MAX;
+  const int cs = gs_chunk(nv);
+  for (int t0 = 0; t0 < nv; t0 += cs) {
+    const int nc = nv - t0 < cs ? nv - t0 : cs;
     const double* Vt = W.V + (int64_t)t0 * W.n;
-    if (t0 + GS_MAX >= nv) g = launch_gs<3>(Vt, W.n, nc, W.y + t0, W.w, W.n, W.partial, s);
+    if (t0 + cs >= nv) g = launch_gs<3>(Vt, W.n, nc, W.y + t0, W.w, W.n, W.partial, s);
     else launch_gs<1>(Vt, W.n, nc, W.y + t0, W.w, W.n, W.partial, s);
   }
   KL(k_reduce<<<1, RED_THREADS, 0, s>>>(W.partial, 1, g, W.hc + nv, 0));
@@ -466,8 +472,9 @@ cpm_status gram_schmidt(int j, int reorth, Work& W, cudaStream_t s) {
       const int g = launch_gs<2>(W.V, W.n, nv, W.y, W.w, W.n, W.partial, s);
       KL(k_reduce_gs<<<nv, RED_THREADS, 0, s>>>(W.partial, g, W.y, W.hc, 1));
     } else {
-      for (int t0 = 0; t0 < nv; t0 += GS_MAX) {
-        const int nc = nv - t0 < GS_MAX ? nv - t0 : GS_MAX;
+      const int cs = gs_chunk(nv);
+      for (int t0 = 0; t0 < nv; t0 += cs) {
+        const int nc = nv - t0 < cs ? nv - t0 : cs;
         launch_gs<1>(W.V + (int64_t)t0 * W.n, W.n, nc, W.y + t0, W.w, W.n, W.partial, s);
       }
       CPM_TRY(gs_dots(nv, true, W, s));
@@ -564,8 +571,9 @@ cpm_status gmres(const Ops& o, const double* f, double* x, int m, int maxit, dou
     KL(k_trisolve<<<1, 1, 0, s>>>(W.H, m, W.g, k, W.y));
     CPM_CUDA(cudaMemsetAsync(W.t, 0, n * sizeof(double), s));
     KL(k_negate<<<1, 256, 0, s>>>(W.y, W.ny, k));
-    for (int t0 = 0; t0 < k; t0 += GS_MAX) {
-      const int nc = k - t0 < GS_MAX ? k - t0 : GS_MAX;
+    const int cs = gs_chunk(k);
+    for (int t0 = 0; t0 < k; t0 += cs) {
+      const int nc = k - t0 < cs ? k - t0 : cs;
       launch_gs<1>(W.V + (int64_t)t0 * n, n, nc, W.ny + t0, W.t, n, nullptr, s);
     }
     CPM_TRY(op_P(o, W.t, W.z, W, s));

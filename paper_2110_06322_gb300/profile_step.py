@@ -7,7 +7,10 @@ no clock sampler, no host oracle, nothing else on the GPU.
 With --setup-only a step is the set-up alone: band build, Schwarz set-up, and
 one transposed operator and preconditioner apply (which build the transpose
 map and the transposed factors on first use), each phase timed with CUDA
-events.
+events.  With --apply-only KIND the band (and for KIND pc the Schwarz
+preconditioner) is built once and a step is one FP32 apply of that kind: op
+(the operator M), opT (its transpose) or pc (the Schwarz preconditioner), for
+captures of those kernels alone.
 """
 from __future__ import annotations
 
@@ -24,6 +27,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--setup-only", action="store_true")
+    ap.add_argument("--apply-only", choices=["op", "opT", "pc"], default=None)
+    ap.add_argument("--maxit", type=int, default=50000,
+                    help="iteration cap of each solve (a short capture of the Krylov loop)")
     a = ap.parse_args()
     w = inputs.WORKLOADS[a.workload]
     L0 = cpm.cpm_kernel_launches()
@@ -34,7 +40,26 @@ def main():
     del B0
     torch.cuda.synchronize()
     print(f"setup launches={cpm.cpm_kernel_launches() - L0}", flush=True)
-    kw = dict(restart=w["restart"], rtol=w["rtol"], maxit=50000, mixed=True, inner_rtol=1e-4, reorth=0)
+    kw = dict(restart=w["restart"], rtol=w["rtol"], maxit=a.maxit, mixed=True, inner_rtol=1e-4, reorth=0)
+    if a.apply_only:
+        B = cpm.Band(w["kind"], w["params"], w["h"], w["p"])
+        x = f.float()
+        y = torch.empty_like(x)
+        if a.apply_only == "pc":
+            P = cpm.Schwarz(B, w["c"], w["nparts"], w["overlap"], robin=w["robin"], store=cpm.CPM_F32)
+            run = lambda: P.apply(x, out=y)  # noqa: E731
+        else:
+            tr = a.apply_only == "opT"
+            run = lambda: B.apply(w["c"], x, transpose=tr, out=y)  # noqa: E731
+        run()  # first use builds the transpose map
+        torch.cuda.synchronize()
+        print(f"setup launches={cpm.cpm_kernel_launches() - L0}", flush=True)
+        for q in range(a.warmup + a.steps):
+            L1 = cpm.cpm_kernel_launches()
+            run()
+            torch.cuda.synchronize()
+            print(f"apply step {q}: launches={cpm.cpm_kernel_launches() - L1}", flush=True)
+        return
     if a.setup_only:
         for q in range(a.warmup + a.steps):
             L0 = cpm.cpm_kernel_launches()
