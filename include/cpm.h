@@ -219,6 +219,47 @@ cpm_status cpm_solve(const cpm_band* band, const oras_pc* pc, double c, const do
 cpm_status cpm_solve_adjoint(const cpm_band* band, const oras_pc* pc, double c, const double* g, double* lambda,
                              const cpm_solve_params* prm, cpm_solve_info* info, void* stream);
 
+/* ------------------------------------------------------------------ reaction-diffusion (IMEX)
+ * Schnakenberg system of eq. schnack (Section 4.1.6) on the band,
+ *   u_t = D_u Delta_S u + delta1 - u + u^2 v + lambda v
+ *   v_t = D_v Delta_S v + delta2 - u^2 v - lambda v,
+ * advanced by semi-implicit Euler steps (diffusion implicit, reaction
+ * explicit): each step solves (c_u I - Delta_S^h) u' = c_u (u + dt f(u, v))
+ * with c_u = 1 / (D_u dt), and the same for v -- two shifted Poisson solves
+ * (cpm_solve with c = c_u, c_v).  The paper's reaction-diffusion examples
+ * treat diffusion implicitly with PETSc's IMEX Runge-Kutta schemes (Section
+ * 4.1.3, Section 4.1.5); the step here is the first-order member of that
+ * family. */
+typedef struct {
+  double delta1, delta2, lambda;  /* reaction parameters (eq. schnack) */
+  double Du, Dv;                  /* diffusion coefficients, > 0 */
+  double dt;                      /* step, > 0 */
+} cpm_schnakenberg;
+
+/* cpm_imex_rhs -- right-hand sides of one step:
+ *   bu = c_u (u + dt f(u, v)),  bv = c_v (v + dt g(u, v)).
+ * u, v, bu, bv: DEVICE, N_A doubles each (bu, bv must not overlap u, v). */
+cpm_status cpm_imex_rhs(const cpm_band* band, const cpm_schnakenberg* prm, const double* u, const double* v,
+                        double* bu, double* bv, void* stream);
+
+/* cpm_imex_rhs_adjoint -- reverse of one step for a loss L of the state after it.
+ *   u, v     state before the step;  u1, v1 state after it (DEVICE, N_A each)
+ *   lu, lv   adjoint solutions M_u^{-T} dL/du1, M_v^{-T} dL/dv1 (DEVICE)
+ *   ubar     = dL/du through this step = c_u lu (1 + dt f_u) + c_v lv dt g_u
+ *   vbar     = dL/dv through this step = c_u lu dt f_v + c_v lv (1 + dt g_v)
+ *   dc       DEVICE, 2 doubles, ACCUMULATED: dc[0] += <lu, u + dt f - u1> and
+ *            dc[1] += <lv, v + dt g - v1>, this step's dL/dc_u and dL/dc_v
+ *            (over all steps, dL/dD_u = -(c_u / D_u) dc[0]).
+ * The sums use a fixed reduction order (reproducible). */
+cpm_status cpm_imex_rhs_adjoint(const cpm_band* band, const cpm_schnakenberg* prm, const double* u, const double* v,
+                                const double* u1, const double* v1, const double* lu, const double* lv,
+                                double* ubar, double* vbar, double* dc, void* stream);
+
+/* cpm_dot -- out[0] = <a, b> over N_A doubles (DEVICE a, b, out), in a fixed
+ * reduction order.  Used by gradients with respect to the shift c
+ * (dL/dc = -<lambda, u> for u = M^{-1} f). */
+cpm_status cpm_dot(const cpm_band* band, const double* a, const double* b, double* out, void* stream);
+
 void cpm_band_free(cpm_band* band);
 void oras_free(oras_pc* pc);
 

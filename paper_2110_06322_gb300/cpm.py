@@ -47,6 +47,11 @@ class cpm_solve_info(C.Structure):
                 ("ms_operator", C.c_double), ("n_precond", C.c_int32), ("n_operator", C.c_int32)]
 
 
+class cpm_schnakenberg(C.Structure):
+    _fields_ = [("delta1", C.c_double), ("delta2", C.c_double), ("lambda_", C.c_double), ("Du", C.c_double),
+                ("Dv", C.c_double), ("dt", C.c_double)]
+
+
 class CpmError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -80,6 +85,9 @@ def lib():
         "oras_free": (None, [vp]),
         "cpm_kernel_launches": (C.c_int64, []),
         "cpm_apply_noalloc": (i32, [vp, P(C.c_double), vp, vp, i32, i32, vp]),
+        "cpm_imex_rhs": (i32, [vp, P(cpm_schnakenberg), vp, vp, vp, vp, vp]),
+        "cpm_imex_rhs_adjoint": (i32, [vp, P(cpm_schnakenberg), vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
+        "cpm_dot": (i32, [vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -91,7 +99,8 @@ def lib():
 
 EXPORTED = ["cpm_last_error", "cpm_band_build", "cpm_band_info", "cpm_band_export", "cpm_band_weights", "cpm_apply",
             "oras_setup", "oras_apply", "oras_info", "oras_export", "cpm_solve", "cpm_solve_adjoint", "cpm_band_free",
-            "oras_free", "cpm_kernel_launches", "cpm_apply_noalloc"]
+            "oras_free", "cpm_kernel_launches", "cpm_apply_noalloc", "cpm_imex_rhs", "cpm_imex_rhs_adjoint",
+            "cpm_dot"]
 
 
 def _check(st):
@@ -141,6 +150,29 @@ def cpm_apply_noalloc(band, c, x, y, stream=None):
     cs = (C.c_double * nrhs)(*([float(c)] * nrhs if not hasattr(c, "__len__") else [float(v) for v in c]))
     _check(lib().cpm_apply_noalloc(band, cs, _ptr(x), _ptr(y), _dtype_code(x), nrhs, _stream(stream)))
     return y
+
+
+def _rx(prm):
+    return cpm_schnakenberg(float(prm["delta1"]), float(prm["delta2"]), float(prm["lambda"]), float(prm["Du"]),
+                            float(prm["Dv"]), float(prm["dt"]))
+
+
+def cpm_imex_rhs(band, prm, u, v, bu, bv, stream=None):
+    """bu = c_u (u + dt f(u, v)), bv = c_v (v + dt g(u, v)); prm: dict with
+    delta1, delta2, lambda, Du, Dv, dt."""
+    _check(lib().cpm_imex_rhs(band, C.byref(_rx(prm)), _ptr(u), _ptr(v), _ptr(bu), _ptr(bv), _stream(stream)))
+    return bu, bv
+
+
+def cpm_imex_rhs_adjoint(band, prm, u, v, u1, v1, lu, lv, ubar, vbar, dc, stream=None):
+    _check(lib().cpm_imex_rhs_adjoint(band, C.byref(_rx(prm)), _ptr(u), _ptr(v), _ptr(u1), _ptr(v1), _ptr(lu),
+                                      _ptr(lv), _ptr(ubar), _ptr(vbar), _ptr(dc), _stream(stream)))
+    return ubar, vbar, dc
+
+
+def cpm_dot(band, a, b, out, stream=None):
+    _check(lib().cpm_dot(band, _ptr(a), _ptr(b), _ptr(out), _stream(stream)))
+    return out
 
 
 def oras_setup(band, c, nparts, overlap, robin=False, alpha=4.0, alpha_cross=20.0, store=CPM_F32, stream=None):

@@ -137,6 +137,38 @@ cpm_status oras_export(const oras_pc* pc, int32_t* part, int64_t* sub_ptr, int32
   return CPM_OK;
 }
 
+static cpm_status check_rx(const cpm_schnakenberg* p) {
+  if (!p) return fail(CPM_ERR_ARG, "null reaction parameters");
+  if (!(p->Du > 0.0) || !(p->Dv > 0.0) || !(p->dt > 0.0))
+    return fail(CPM_ERR_ARG, "Du, Dv and dt must be > 0");
+  if (!std::isfinite(p->delta1) || !std::isfinite(p->delta2) || !std::isfinite(p->lambda) || !std::isfinite(p->Du) ||
+      !std::isfinite(p->Dv) || !std::isfinite(p->dt))
+    return fail(CPM_ERR_NAN, "reaction parameters must be finite");
+  return CPM_OK;
+}
+
+cpm_status cpm_imex_rhs(const cpm_band* band, const cpm_schnakenberg* prm, const double* u, const double* v,
+                        double* bu, double* bv, void* stream) {
+  if (!band || !u || !v || !bu || !bv) return fail(CPM_ERR_ARG, "null argument");
+  if (bu == u || bu == v || bv == u || bv == v || bu == bv) return fail(CPM_ERR_ARG, "outputs must not alias inputs");
+  CPM_TRY(check_rx(prm));
+  return imex_rhs(prm, band->nA, u, v, bu, bv, as_stream(stream));
+}
+
+cpm_status cpm_imex_rhs_adjoint(const cpm_band* band, const cpm_schnakenberg* prm, const double* u, const double* v,
+                                const double* u1, const double* v1, const double* lu, const double* lv,
+                                double* ubar, double* vbar, double* dc, void* stream) {
+  if (!band || !u || !v || !u1 || !v1 || !lu || !lv || !ubar || !vbar || !dc)
+    return fail(CPM_ERR_ARG, "null argument");
+  CPM_TRY(check_rx(prm));
+  return imex_rhs_adjoint(prm, band->nA, u, v, u1, v1, lu, lv, ubar, vbar, dc, as_stream(stream));
+}
+
+cpm_status cpm_dot(const cpm_band* band, const double* a, const double* b, double* out, void* stream) {
+  if (!band || !a || !b || !out) return fail(CPM_ERR_ARG, "null argument");
+  return dot(band->nA, a, b, out, as_stream(stream));
+}
+
 cpm_status cpm_solve(const cpm_band* band, const oras_pc* pc, double c, const double* f, double* u,
                      const cpm_solve_params* prm, cpm_solve_info* info, void* stream) {
   if (!band || !f || !u || !prm || !info) return fail(CPM_ERR_ARG, "null argument");

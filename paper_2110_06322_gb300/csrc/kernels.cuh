@@ -26,4 +26,12 @@ cpm_status build_transpose_map(cpm_band* B, cudaStream_t s);
 cpm_status apply_op_scratch(const cpm_band* B, const double* c, const void* x, void* y, cpm_dtype dt, int nrhs,
                             void* scratch, cudaStream_t s);
 
+// imex.cu: reaction-diffusion step right-hand sides, their adjoint, dot product
+cpm_status imex_rhs(const cpm_schnakenberg* prm, int64_t n, const double* u, const double* v, double* bu, double* bv,
+                    cudaStream_t s);
+cpm_status imex_rhs_adjoint(const cpm_schnakenberg* prm, int64_t n, const double* u, const double* v,
+                            const double* u1, const double* v1, const double* lu, const double* lv, double* ubar,
+                            double* vbar, double* dc, cudaStream_t s);
+cpm_status dot(int64_t n, const double* a, const double* b, double* out, cudaStream_t s);
+
 }  // namespace cpm
