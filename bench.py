@@ -42,10 +42,10 @@ from paper_2110_06322_gb300 import inputs  # noqa: E402
 WORKLOAD = "torus_h0.004"
 SAMPLE = dict(h=0.025, nparts=16)  # oracle sample: same torus, same subdomain size
 # DRAM bytes per stored factor entry of one FP32 Schwarz apply (dram__bytes_read.sum + dram__bytes_write.sum
-# of one ncu capture on the torus h = 0.0125 / 64-part case, 564.23 MB over 88,019,898 entries; summary in
+# of one ncu capture on the torus h = 0.0125 / 64-part case, 564.35 MB over 88,019,898 entries; summary in
 # profiles/k_schwarz_pk_fp32_torus_h0.0125.md).  Traffic grows with the stored entries, so a full launch moves
 # this times Sigma nnz(A_j).  Re-measure when k_schwarz_pk changes.
-SCHWARZ_TRAFFIC_PER_ENTRY = 564.226048e6 / 88019898
+SCHWARZ_TRAFFIC_PER_ENTRY = 564.354048e6 / 88019898
 METRIC = "ORAS-GMRES band-pt*iters/s (full pipeline: band, set-up, mixed forward + adjoint solve at 1e-8)"
 UNIT = "band-pt*iters/s"
 

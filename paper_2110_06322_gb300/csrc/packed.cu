@@ -39,7 +39,7 @@ namespace {
 
 constexpr int CHUNK_BYTES = 24576;
 constexpr int NSTAGE = 2;
-constexpr int PK_WARPS = 24;
+constexpr int PK_WARPS = 12;
 constexpr unsigned WAIT_LIMIT = 1u << 22;  // polls of one mbarrier before giving up (seconds at most)
 
 __host__ __device__ inline int64_t pad16(int64_t b) { return (b + 15) & ~(int64_t)15; }

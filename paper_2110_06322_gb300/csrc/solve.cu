@@ -10,6 +10,7 @@
 //
 // All reductions are two-stage with a fixed grid and a fixed summation order,
 // so a solve is bitwise reproducible on the same device.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -275,7 +276,8 @@ struct Work {
   float *v32 = nullptr, *z32 = nullptr, *w32 = nullptr;
   double *H = nullptr, *hc = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr, *ny = nullptr;
   double *partial = nullptr, *scal = nullptr;  // partial: (32 + 1) x RED_BLOCKS
-  double* pub = nullptr;  // pinned host
+  double* pub = nullptr;  // pinned host: two slots of {|g_{j+1}|, h_{j+1,j}, 1/h_{j+1,j}} at 0 and 4
+  cudaEvent_t ev[2] = {nullptr, nullptr};  // iteration j's slot has landed
   cpm_status alloc(int64_t n_, int m_, bool f32, cudaStream_t s) {
     n = n_;
     m = m_;
@@ -299,6 +301,7 @@ struct Work {
     CPM_TRY(dalloc(&partial, (size_t)(32 + 1) * RED_BLOCKS, s));
     CPM_TRY(dalloc(&scal, 8, s));
     CPM_CUDA(cudaMallocHost((void**)&pub, 8 * sizeof(double)));
+    for (int q = 0; q < 2; ++q) CPM_CUDA(cudaEventCreateWithFlags(&ev[q], cudaEventDisableTiming));
     return CPM_OK;
   }
   void release(cudaStream_t s) {
@@ -308,6 +311,9 @@ struct Work {
     dfree(w32, s);
     if (pub) cudaFreeHost(pub);
     pub = nullptr;
+    for (int q = 0; q < 2; ++q)
+      if (ev[q]) cudaEventDestroy(ev[q]);
+    ev[0] = ev[1] = nullptr;
   }
 };
 
@@ -548,25 +554,40 @@ cpm_status gmres(const Ops& o, const double* f, double* x, int m, int maxit, dou
     KL(k_rsqrt1<<<1, 32, 0, s>>>(W.scal + 1, W.scal + 5));
     KL(k_scale<<<G, 256, 0, s>>>(W.r, W.scal + 5, W.V, n));
     KL(k_init_g<<<1, 256, 0, s>>>(W.g, m, W.scal + 1));
+    // Iteration j's residual estimate is read on the host while iteration j+1
+    // already runs (the host waits on j's event after queueing j+1), so the
+    // GPU never idles on the convergence test.  When the test stops the cycle
+    // at j, the speculative iteration j+1 is discarded: k = j + 1 columns are
+    // used, and nothing of column j+1 (its H column, its rotation, g[j+2])
+    // enters the least-squares solution.
     int k = 0;
-    for (int j = 0; j < m && out.iters < maxit; ++j) {
-      double* vj = W.V + (int64_t)j * n;
-      CPM_TRY(op_MP(o, vj, W.w, W, s));
-      CPM_TRY(gram_schmidt(j, reorth, W, s));
-      KL(k_givens<<<1, 1, 0, s>>>(W.H, m, W.hc, W.cs, W.sn, W.g, j, W.scal + 2));
-      CPM_CUDA(cudaMemcpyAsync(W.pub, W.scal + 2, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
-      CPM_CUDA(cudaStreamSynchronize(s));
-      CPM_CUDA(cudaGetLastError());
-      out.iters++;
+    const int jmax = std::min(m, maxit - out.iters);
+    auto check = [&](int j, bool& stop) -> cpm_status {
+      CPM_CUDA(cudaEventSynchronize(W.ev[j & 1]));
+      const double* pj = W.pub + 4 * (j & 1);
+      const double est = pj[0], hn = pj[1];
       k = j + 1;
-      const double est = W.pub[0], hn = W.pub[1];
       if (!std::isfinite(est)) {
         out.status = CPM_ERR_NAN;
         return fail(CPM_ERR_NAN, "Krylov iteration produced NaN or Inf");
       }
-      if (hn == 0.0 || est <= rtol * fn) break;
+      stop = hn == 0.0 || est <= rtol * fn;
+      return CPM_OK;
+    };
+    bool stop = false;
+    for (int j = 0; j < jmax && !stop; ++j) {
+      double* vj = W.V + (int64_t)j * n;
+      CPM_TRY(op_MP(o, vj, W.w, W, s));
+      CPM_TRY(gram_schmidt(j, reorth, W, s));
+      KL(k_givens<<<1, 1, 0, s>>>(W.H, m, W.hc, W.cs, W.sn, W.g, j, W.scal + 2));
+      CPM_CUDA(cudaMemcpyAsync(W.pub + 4 * (j & 1), W.scal + 2, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CPM_CUDA(cudaEventRecord(W.ev[j & 1], s));
       if (j + 1 < m) KL(k_scale<<<G, 256, 0, s>>>(W.w, W.scal + 4, W.V + (int64_t)(j + 1) * n, n));
+      CPM_CUDA(cudaGetLastError());
+      if (j > 0) CPM_TRY(check(j - 1, stop));
     }
+    if (!stop && jmax > 0) CPM_TRY(check(jmax - 1, stop));
+    out.iters += k;
     // x += P (V y)
     KL(k_trisolve<<<1, 1, 0, s>>>(W.H, m, W.g, k, W.y));
     CPM_CUDA(cudaMemsetAsync(W.t, 0, n * sizeof(double), s));
