@@ -28,17 +28,21 @@ import torch
 from . import cpm
 
 
-def _fwd_solve(band, pc, c, f, opts):
+def _fwd_solve(band, pc, c, f, opts, tally=None):
     u, info = cpm.solve(band, f.contiguous(), pc, c=float(c), **opts)
     if info["status"] != cpm.CPM_OK:
         raise cpm.CpmError(info["status"], f"solve did not reach rtol: {info}")
+    if tally is not None:
+        tally.append(info["iters"])
     return u
 
 
-def _adj_solve(band, pc, c, g, opts):
+def _adj_solve(band, pc, c, g, opts, tally=None):
     lam, info = cpm.solve(band, g.contiguous(), pc, c=float(c), adjoint=True, **opts)
     if info["status"] != cpm.CPM_OK:
         raise cpm.CpmError(info["status"], f"adjoint solve did not reach rtol: {info}")
+    if tally is not None:
+        tally.append(info["iters"])
     return lam
 
 
@@ -89,6 +93,7 @@ class Schnakenberg:
         self.opts.update(solve_opts)
         self._pcs = {}
         self.solves = 0
+        self.iters = []  # GMRES iterations of every solve, in order
 
     def steady_state(self):
         u = self.delta1 + self.delta2
@@ -113,8 +118,8 @@ class Schnakenberg:
         cu, cv = self.shifts(Du, Dv)
         bu, bv = torch.empty_like(u), torch.empty_like(v)
         cpm.cpm_imex_rhs(self.band.handle, prm, u, v, bu, bv)
-        u1 = _fwd_solve(self.band, self._pc(cu), cu, bu, self.opts)
-        v1 = _fwd_solve(self.band, self._pc(cv), cv, bv, self.opts)
+        u1 = _fwd_solve(self.band, self._pc(cu), cu, bu, self.opts, self.iters)
+        v1 = _fwd_solve(self.band, self._pc(cv), cv, bv, self.opts, self.iters)
         self.solves += 2
         return u1, v1
 
@@ -160,8 +165,8 @@ class _ImexRun(torch.autograd.Function):
                 states.append(sim.step(*states[-1], du, dv))
             for n in range(end - 1, start - 1, -1):
                 (u, v), (u1, v1) = states[n - start], states[n - start + 1]
-                lu = _adj_solve(band, pu, cu, ub, sim.opts)
-                lv = _adj_solve(band, pv, cv, vb, sim.opts)
+                lu = _adj_solve(band, pu, cu, ub, sim.opts, sim.iters)
+                lv = _adj_solve(band, pv, cv, vb, sim.opts, sim.iters)
                 sim.solves += 2
                 ub, vb = torch.empty_like(u), torch.empty_like(v)
                 cpm.cpm_imex_rhs_adjoint(band.handle, prm, u, v, u1, v1, lu, lv, ub, vb, dcs)

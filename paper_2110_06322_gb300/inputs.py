@@ -79,6 +79,11 @@ WORKLOADS = {
     "torus_h0.002": dict(kind=TORUS, params=surface_params(TORUS, a=1.0, b=0.4), h=0.002, p=3, c=10.0,
                          rhs="modes", seed=3, nparts=512, overlap=2, robin=False, alpha=4.0, alpha_cross=20.0,
                          restart=30, rtol=1e-8),
+    # differentiable Schnakenberg run (eq. schnack): D = (1e-3, 1e-1), dt = 0.01, 500 steps, state
+    # checkpoints every 25 steps; initial state (u*, v*) (1 + 0.01 U[-1, 1]) from seed 7 (u) and 8 (v)
+    "schnakenberg_torus_h0.005": dict(kind=TORUS, params=surface_params(TORUS, a=1.0, b=0.4), h=0.005, p=3,
+                                      Du=1e-3, Dv=1e-1, dt=0.01, steps=500, checkpoint=25, seed=7, nparts=256,
+                                      overlap=2, robin=False, restart=30, rtol=1e-10),
 }
 
 
