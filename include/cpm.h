@@ -219,6 +219,30 @@ cpm_status cpm_solve(const cpm_band* band, const oras_pc* pc, double c, const do
 cpm_status cpm_solve_adjoint(const cpm_band* band, const oras_pc* pc, double c, const double* g, double* lambda,
                              const cpm_solve_params* prm, cpm_solve_info* info, void* stream);
 
+/* cpm_solve_batch -- solve many independent systems in lockstep: problem p
+ * (p < nprob) has its own band, preconditioner pcs[p] (NULL: none; pcs may
+ * be NULL for none anywhere) and shift c[p] (HOST array), and nrhs[p] >= 1
+ * right-hand sides, each solved with the same GMRES(restart) as cpm_solve
+ * (one classical Gram-Schmidt pass; prm->reorth is not used).
+ *   f, u   DEVICE, the concatenation over p of nrhs[p] x N_A(p) doubles
+ *          (problem-major, right-hand side within problem); u holds the
+ *          initial guesses on entry and the solutions on exit.
+ *   info   HOST array of sum(nrhs) entries, one per system in that order.
+ *   transpose  1: solve the adjoint systems M^T u = f.
+ * Every iteration applies the operator and the preconditioner once per
+ * problem for all its right-hand sides; the Krylov vector work runs over the
+ * whole batch in single launches with per-system reductions.  A system stops
+ * on the device when its residual estimate reaches rtol |f| and is frozen
+ * until the others finish their cycle; each cycle ends with every system's
+ * true FP64 residual.  mixed = 1 runs the operator and preconditioner in FP32
+ * inside FP64 iterative refinement (FP32 or BF16 factors required).
+ * Returns CPM_ERR_NOT_CONVERGED if any system missed rtol within maxit
+ * iterations (its info[] entry says which).  Synchronises the stream.
+ * The paper solves one problem per PETSc run; batching is this library's. */
+cpm_status cpm_solve_batch(int32_t nprob, const cpm_band* const* bands, const oras_pc* const* pcs, const double* c,
+                           const int32_t* nrhs, const double* f, double* u, const cpm_solve_params* prm,
+                           cpm_solve_info* info, int32_t transpose, void* stream);
+
 /* ------------------------------------------------------------------ reaction-diffusion (IMEX)
  * Schnakenberg system of eq. schnack (Section 4.1.6) on the band,
  *   u_t = D_u Delta_S u + delta1 - u + u^2 v + lambda v

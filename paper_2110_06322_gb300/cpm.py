@@ -88,6 +88,8 @@ def lib():
         "cpm_imex_rhs": (i32, [vp, P(cpm_schnakenberg), vp, vp, vp, vp, vp]),
         "cpm_imex_rhs_adjoint": (i32, [vp, P(cpm_schnakenberg), vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
         "cpm_dot": (i32, [vp, vp, vp, vp, vp]),
+        "cpm_solve_batch": (i32, [i32, vp, vp, P(C.c_double), P(C.c_int32), vp, vp, P(cpm_solve_params),
+                                  P(cpm_solve_info), i32, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -100,7 +102,7 @@ def lib():
 EXPORTED = ["cpm_last_error", "cpm_band_build", "cpm_band_info", "cpm_band_export", "cpm_band_weights", "cpm_apply",
             "oras_setup", "oras_apply", "oras_info", "oras_export", "cpm_solve", "cpm_solve_adjoint", "cpm_band_free",
             "oras_free", "cpm_kernel_launches", "cpm_apply_noalloc", "cpm_imex_rhs", "cpm_imex_rhs_adjoint",
-            "cpm_dot"]
+            "cpm_dot", "cpm_solve_batch"]
 
 
 def _check(st):
@@ -205,6 +207,32 @@ def cpm_solve(band, pc, c, f, u, restart=30, maxit=10000, rtol=1e-8, mixed=False
             "n_precond": info.n_precond, "n_operator": info.n_operator}
 
 
+def _info_dict(st, info):
+    return {"status": st, "iters": info.iters, "restarts": info.restarts, "ir_steps": info.ir_steps,
+            "rel_residual": info.rel_residual, "ms_precond": info.ms_precond, "ms_operator": info.ms_operator,
+            "n_precond": info.n_precond, "n_operator": info.n_operator}
+
+
+def cpm_solve_batch(bands, pcs, c, nrhs, f, u, restart=30, maxit=10000, rtol=1e-8, mixed=False, inner_rtol=1e-4,
+                    adjoint=False, stream=None):
+    """Lockstep GMRES over len(bands) problems (band handles, preconditioner
+    handles or None, shifts, right-hand-side counts); f, u: concatenated
+    device vectors.  Returns (status, [info per system])."""
+    P = len(bands)
+    hb = (C.c_void_p * P)(*[b.value if isinstance(b, C.c_void_p) else b for b in bands])
+    hp = (C.c_void_p * P)(*[(q.value if isinstance(q, C.c_void_p) else q) if q is not None else None for q in pcs])
+    hc = (C.c_double * P)(*[float(x) for x in c])
+    hn = (C.c_int32 * P)(*[int(x) for x in nrhs])
+    S = sum(int(x) for x in nrhs)
+    infos = (cpm_solve_info * S)()
+    prm = cpm_solve_params(int(restart), int(maxit), float(rtol), int(bool(mixed)), 0, float(inner_rtol), 0)
+    st = lib().cpm_solve_batch(P, hb, hp, hc, hn, _ptr(f), _ptr(u), C.byref(prm), infos, int(bool(adjoint)),
+                               _stream(stream))
+    if st not in (CPM_OK, CPM_ERR_NOT_CONVERGED):
+        _check(st)
+    return st, [_info_dict(infos[q].status, infos[q]) for q in range(S)]
+
+
 def cpm_kernel_launches():
     return lib().cpm_kernel_launches()
 
@@ -290,6 +318,28 @@ class Schwarz:
         nodes = torch.empty(max(self.total_rows, 1), dtype=torch.int32, device=d)
         _check(lib().oras_export(self.handle, _ptr(part), _ptr(sptr), _ptr(nodes), _stream(stream)))
         return part, sptr, nodes[: self.total_rows]
+
+
+def solve_batch(problems, rhs, u0=None, adjoint=False, **kw):
+    """Solve a batch: problems is a list of (Band, Schwarz or None, c); rhs a
+    list of FP64 CUDA tensors, one per problem, of shape (N_A,) or
+    (nrhs, N_A).  Returns (solutions shaped like rhs, [info per system])."""
+    shapes = [t.shape for t in rhs]
+    nrhs = [1 if t.dim() == 1 else t.shape[0] for t in rhs]
+    f = torch.cat([t.reshape(-1) for t in rhs]).contiguous()
+    u = torch.zeros_like(f) if u0 is None else torch.cat([t.reshape(-1) for t in u0]).contiguous()
+    bands = [b.handle for b, _, _ in problems]
+    pcs = [p.handle if p is not None else None for _, p, _ in problems]
+    cs = [float(c) for _, _, c in problems]
+    st, infos = cpm_solve_batch(bands, pcs, cs, nrhs, f, u, adjoint=adjoint, **kw)
+    out, o = [], 0
+    for sh in shapes:
+        k = 1
+        for d in sh:
+            k *= d
+        out.append(u[o:o + k].reshape(sh))
+        o += k
+    return out, infos
 
 
 def solve(band, f, pc=None, c=None, u0=None, adjoint=False, **kw):

@@ -137,6 +137,26 @@ cpm_status oras_export(const oras_pc* pc, int32_t* part, int64_t* sub_ptr, int32
   return CPM_OK;
 }
 
+cpm_status cpm_solve_batch(int32_t nprob, const cpm_band* const* bands, const oras_pc* const* pcs, const double* c,
+                           const int32_t* nrhs, const double* f, double* u, const cpm_solve_params* prm,
+                           cpm_solve_info* info, int32_t transpose, void* stream) {
+  if (nprob < 1 || !bands || !c || !nrhs || !f || !u || !prm || !info) return fail(CPM_ERR_ARG, "null argument");
+  if (prm->restart < 1 || prm->restart > 256 || prm->maxit < 0 || !(prm->rtol > 0.0))
+    return fail(CPM_ERR_ARG, "restart in [1, 256], maxit >= 0 and rtol > 0 required");
+  int64_t S = 0;
+  for (int p = 0; p < nprob; ++p) {
+    if (!bands[p]) return fail(CPM_ERR_ARG, "null band for problem %d", p);
+    if (nrhs[p] < 1) return fail(CPM_ERR_ARG, "nrhs[%d] must be >= 1", p);
+    if (!std::isfinite(c[p])) return fail(CPM_ERR_NAN, "shift c[%d] is not finite", p);
+    if (pcs && pcs[p] && pcs[p]->band != bands[p]) return fail(CPM_ERR_ARG, "pcs[%d] belongs to another band", p);
+    S += nrhs[p];
+  }
+  if (S > 65535) return fail(CPM_ERR_ARG, "at most 65535 systems per batch");
+  if (f == u) return fail(CPM_ERR_ARG, "f and u must not overlap");
+  g_err[0] = 0;
+  return solve_batch(nprob, bands, pcs, c, nrhs, f, u, prm, info, transpose ? 1 : 0, as_stream(stream));
+}
+
 static cpm_status check_rx(const cpm_schnakenberg* p) {
   if (!p) return fail(CPM_ERR_ARG, "null reaction parameters");
   if (!(p->Du > 0.0) || !(p->Dv > 0.0) || !(p->dt > 0.0))

@@ -26,6 +26,11 @@ cpm_status build_transpose_map(cpm_band* B, cudaStream_t s);
 cpm_status apply_op_scratch(const cpm_band* B, const double* c, const void* x, void* y, cpm_dtype dt, int nrhs,
                             void* scratch, cudaStream_t s);
 
+// batch.cu: lockstep GMRES over many systems
+cpm_status solve_batch(int nprob, const cpm_band* const* bands, const oras_pc* const* pcs, const double* c,
+                       const int32_t* nrhs, const double* f, double* u, const cpm_solve_params* prm,
+                       cpm_solve_info* info, int transpose, cudaStream_t s);
+
 // imex.cu: reaction-diffusion step right-hand sides, their adjoint, dot product
 cpm_status imex_rhs(const cpm_schnakenberg* prm, int64_t n, const double* u, const double* v, double* bu, double* bv,
                     cudaStream_t s);
