@@ -21,7 +21,8 @@
 // (FP64), as in the single-system solver.
 //
 // The operator and the preconditioner apply once per problem per iteration,
-// with all its right-hand sides in one launch.  With mixed = 1 they run in
+// with all its right-hand sides in one launch; the problems' launches go to
+// eight side streams, so that small problems run side by side.  With mixed = 1 they run in
 // FP32 inside FP64 iterative refinement (one inner cycle per refinement
 // step), exactly as cpm_solve does for one system.
 #include <algorithm>
@@ -41,11 +42,16 @@ namespace {
 constexpr int BGS = 16;  // basis vectors per segmented Gram-Schmidt kernel
 
 // Block b of a batched vector kernel covers elements [lo[b], hi[b]) of the
-// concatenated vector, all inside system sys[b].
+// concatenated vector, all inside system sys[b].  When act is set, blocks of
+// systems with act[sys] == 0 (stopped) skip their elements: their partial
+// sums are zero and their vectors are left as they are (nothing reads them
+// any more in this cycle).
 struct Seg {
   const int32_t* sys;
   const int64_t* lo;
   const int64_t* hi;
+  const int32_t* act;
+  __device__ __forceinline__ bool skip(int b) const { return act && !act[sys[b]]; }
 };
 
 // partial[t * gridDim.x + b] = block b's share of <V_t, w>, t < nv
@@ -55,7 +61,7 @@ __global__ void __launch_bounds__(RED_THREADS)
   double acc[NV];
 #pragma unroll
   for (int t = 0; t < NV; ++t) acc[t] = 0;
-  const int64_t lo = G.lo[blockIdx.x], hi = G.hi[blockIdx.x];
+  const int64_t lo = G.lo[blockIdx.x], hi = G.skip(blockIdx.x) ? lo : G.hi[blockIdx.x];
   for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
     const double wi = w[i];
 #pragma unroll
@@ -75,7 +81,7 @@ __global__ void __launch_bounds__(RED_THREADS)
   if (threadIdx.x < NV) cf[threadIdx.x] = threadIdx.x < nv ? coef[(int64_t)s * ldc + threadIdx.x] : 0.0;
   __syncthreads();
   double acc[1] = {0.0};
-  const int64_t lo = G.lo[blockIdx.x], hi = G.hi[blockIdx.x];
+  const int64_t lo = G.lo[blockIdx.x], hi = G.skip(blockIdx.x) ? lo : G.hi[blockIdx.x];
   for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
     double wi = w[i];
 #pragma unroll
@@ -107,7 +113,7 @@ __global__ void __launch_bounds__(RED_THREADS)
 __global__ void __launch_bounds__(RED_THREADS)
     kb_scale(Seg G, const double* __restrict__ w, const double* __restrict__ scale, double* v) {
   const double a = scale[G.sys[blockIdx.x]];
-  const int64_t lo = G.lo[blockIdx.x], hi = G.hi[blockIdx.x];
+  const int64_t lo = G.lo[blockIdx.x], hi = G.skip(blockIdx.x) ? lo : G.hi[blockIdx.x];
   for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) v[i] = w[i] * a;
 }
 
@@ -226,7 +232,47 @@ struct Batch {
   std::vector<int> nrhs;
   std::vector<int64_t> po;  // problem offsets [P+1]
   std::vector<char> live;   // problems with a system still iterating (this cycle)
-  Seg G{};
+  std::vector<char> zeroed; // finished problems whose z and w segments are zero
+  // side streams: the per-problem operator and preconditioner launches of one
+  // iteration run concurrently (small problems fill only a few SMs each)
+  static constexpr int NSTREAM = 8;
+  cudaStream_t ss[NSTREAM] = {};
+  cudaEvent_t fork = nullptr, join[NSTREAM] = {};
+  cpm_status make_streams() {
+    for (int k = 0; k < NSTREAM; ++k) {
+      CPM_CUDA(cudaStreamCreateWithFlags(&ss[k], cudaStreamNonBlocking));
+      CPM_CUDA(cudaEventCreateWithFlags(&join[k], cudaEventDisableTiming));
+    }
+    CPM_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    return CPM_OK;
+  }
+  void free_streams() {
+    for (int k = 0; k < NSTREAM; ++k) {
+      if (ss[k]) cudaStreamDestroy(ss[k]);
+      if (join[k]) cudaEventDestroy(join[k]);
+      ss[k] = nullptr;
+      join[k] = nullptr;
+    }
+    if (fork) cudaEventDestroy(fork);
+    fork = nullptr;
+  }
+  // side streams start after everything queued on s so far
+  cpm_status fan_out(cudaStream_t s) {
+    CPM_CUDA(cudaEventRecord(fork, s));
+    for (int k = 0; k < NSTREAM; ++k) CPM_CUDA(cudaStreamWaitEvent(ss[k], fork, 0));
+    return CPM_OK;
+  }
+  // s continues after all side-stream work
+  cpm_status fan_in(cudaStream_t s) {
+    for (int k = 0; k < NSTREAM; ++k) {
+      CPM_CUDA(cudaEventRecord(join[k], ss[k]));
+      CPM_CUDA(cudaStreamWaitEvent(s, join[k], 0));
+    }
+    return CPM_OK;
+  }
+  cudaStream_t side(int p) const { return ss[p % NSTREAM]; }
+  Seg G{};   // every block works
+  Seg GA{};  // blocks of stopped systems skip (act = X.active)
   int32_t* sb = nullptr;  // [S+1] first block of each system
   double *V = nullptr, *w = nullptr, *z = nullptr, *t = nullptr, *r = nullptr, *ny = nullptr, *partial = nullptr;
   float *x32 = nullptr, *y32 = nullptr;
@@ -242,6 +288,7 @@ struct Batch {
   void release(cudaStream_t s) {
     for (void* p : owned) cudaFreeAsync(p, s);
     owned.clear();
+    free_streams();
   }
 };
 
@@ -285,7 +332,7 @@ cpm_status make_segments(Batch& Bt, const std::vector<int64_t>& so, cudaStream_t
   CPM_CUDA(cudaMemcpyAsync(dhi, hi.data(), NB * sizeof(int64_t), cudaMemcpyHostToDevice, s));
   CPM_CUDA(cudaMemcpyAsync(dsb, sb.data(), (S + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, s));
   CPM_CUDA(cudaStreamSynchronize(s));  // the host vectors go out of scope
-  Bt.G = Seg{dsys, dlo, dhi};
+  Bt.G = Seg{dsys, dlo, dhi, nullptr};
   Bt.sb = dsb;
   return CPM_OK;
 }
@@ -293,23 +340,23 @@ cpm_status make_segments(Batch& Bt, const std::vector<int64_t>& so, cudaStream_t
 int grid_n(int64_t n) { return grid_for(n, 256); }
 
 // partial sums and per-system reductions of <V_t, w>, t in [t0, t0 + nc)
-cpm_status seg_dots(Batch& Bt, const double* V, int nc, const double* w, double* out, int ldo, int acc,
-                    cudaStream_t s) {
-  if (nc <= 8) KL(kb_dots<8><<<Bt.NB, RED_THREADS, 0, s>>>(Bt.G, V, Bt.N, nc, w, Bt.partial));
-  else KL(kb_dots<16><<<Bt.NB, RED_THREADS, 0, s>>>(Bt.G, V, Bt.N, nc, w, Bt.partial));
+cpm_status seg_dots(Batch& Bt, const Seg& G, const double* V, int nc, const double* w, double* out, int ldo,
+                    int acc, cudaStream_t s) {
+  if (nc <= 8) KL(kb_dots<8><<<Bt.NB, RED_THREADS, 0, s>>>(G, V, Bt.N, nc, w, Bt.partial));
+  else KL(kb_dots<16><<<Bt.NB, RED_THREADS, 0, s>>>(G, V, Bt.N, nc, w, Bt.partial));
   KL(kb_reduce<<<dim3(nc, Bt.S), RED_THREADS, 0, s>>>(Bt.partial, Bt.NB, Bt.sb, out, ldo, acc));
   return CPM_OK;
 }
 
 // w -= V_{t0..t0+nc} coef; with norm, out[s * ldo] = |w_s|^2
-cpm_status seg_update(Batch& Bt, const double* V, int nc, const double* coef, int ldc, double* w, bool norm,
-                      double* out, int ldo, cudaStream_t s) {
+cpm_status seg_update(Batch& Bt, const Seg& G, const double* V, int nc, const double* coef, int ldc, double* w,
+                      bool norm, double* out, int ldo, cudaStream_t s) {
   if (nc <= 8) {
-    if (norm) KL(kb_update<8, true><<<Bt.NB, RED_THREADS, 0, s>>>(Bt.G, V, Bt.N, nc, coef, ldc, w, Bt.partial));
-    else KL(kb_update<8, false><<<Bt.NB, RED_THREADS, 0, s>>>(Bt.G, V, Bt.N, nc, coef, ldc, w, nullptr));
+    if (norm) KL(kb_update<8, true><<<Bt.NB, RED_THREADS, 0, s>>>(G, V, Bt.N, nc, coef, ldc, w, Bt.partial));
+    else KL(kb_update<8, false><<<Bt.NB, RED_THREADS, 0, s>>>(G, V, Bt.N, nc, coef, ldc, w, nullptr));
   } else {
-    if (norm) KL(kb_update<16, true><<<Bt.NB, RED_THREADS, 0, s>>>(Bt.G, V, Bt.N, nc, coef, ldc, w, Bt.partial));
-    else KL(kb_update<16, false><<<Bt.NB, RED_THREADS, 0, s>>>(Bt.G, V, Bt.N, nc, coef, ldc, w, nullptr));
+    if (norm) KL(kb_update<16, true><<<Bt.NB, RED_THREADS, 0, s>>>(G, V, Bt.N, nc, coef, ldc, w, Bt.partial));
+    else KL(kb_update<16, false><<<Bt.NB, RED_THREADS, 0, s>>>(G, V, Bt.N, nc, coef, ldc, w, nullptr));
   }
   if (norm) KL(kb_reduce<<<dim3(1, Bt.S), RED_THREADS, 0, s>>>(Bt.partial, Bt.NB, Bt.sb, out, ldo, 0));
   return CPM_OK;
@@ -321,47 +368,49 @@ inline int chunk_of(int nv) {
 }
 
 // out = M x per problem (FP64, or FP32 through the conversion buffers).
-// Problems with no live system get out = 0 instead (their x is zero), so a
-// batch does not keep paying for the systems that have finished.
+// Problems with no live system are skipped: the solver zeroes their segments
+// of the outputs (z, w) once when they finish, and nothing else writes them,
+// so a batch does not keep paying for the systems that have finished.
 cpm_status batch_M(Batch& Bt, const double* x, double* out, bool f32, int transpose, cudaStream_t s,
                    bool all = false) {
-  if (f32) KL(kb_d2f<<<grid_n(Bt.N), 256, 0, s>>>(x, Bt.x32, Bt.N));
+  CPM_TRY(Bt.fan_out(s));
   for (int p = 0; p < Bt.P; ++p) {
+    cudaStream_t sp = Bt.side(p);
     std::vector<double> cs(Bt.nrhs[p], Bt.c[p]);
-    const int64_t o = Bt.po[p];
-    if (!all && !Bt.live[p]) {
-      if (f32) CPM_CUDA(cudaMemsetAsync(Bt.y32 + o, 0, (Bt.po[p + 1] - o) * sizeof(float), s));
-      else CPM_CUDA(cudaMemsetAsync(out + o, 0, (Bt.po[p + 1] - o) * sizeof(double), s));
-      continue;
+    const int64_t o = Bt.po[p], len = Bt.po[p + 1] - o;
+    if (!all && !Bt.live[p]) continue;  // its output segment was zeroed when it finished
+    if (f32) {
+      KL(kb_d2f<<<grid_n(len), 256, 0, sp>>>(x + o, Bt.x32 + o, len));
+      CPM_TRY(apply_op(Bt.band[p], cs.data(), Bt.x32 + o, Bt.y32 + o, CPM_F32, Bt.nrhs[p], transpose, sp));
+      KL(kb_f2d<<<grid_n(len), 256, 0, sp>>>(Bt.y32 + o, out + o, len));
+    } else {
+      CPM_TRY(apply_op(Bt.band[p], cs.data(), x + o, out + o, CPM_F64, Bt.nrhs[p], transpose, sp));
     }
-    if (f32) CPM_TRY(apply_op(Bt.band[p], cs.data(), Bt.x32 + o, Bt.y32 + o, CPM_F32, Bt.nrhs[p], transpose, s));
-    else CPM_TRY(apply_op(Bt.band[p], cs.data(), x + o, out + o, CPM_F64, Bt.nrhs[p], transpose, s));
   }
-  if (f32) KL(kb_f2d<<<grid_n(Bt.N), 256, 0, s>>>(Bt.y32, out, Bt.N));
-  return CPM_OK;
+  return Bt.fan_in(s);
 }
 
 // out = P x per problem (identity where a problem has no preconditioner;
-// zero for problems with no live system)
+// zero for problems with no live system); conversions per live problem
 cpm_status batch_P(Batch& Bt, const double* x, double* out, bool f32, int transpose, cudaStream_t s) {
-  if (f32) KL(kb_d2f<<<grid_n(Bt.N), 256, 0, s>>>(x, Bt.x32, Bt.N));
+  CPM_TRY(Bt.fan_out(s));
   for (int p = 0; p < Bt.P; ++p) {
+    cudaStream_t sp = Bt.side(p);
     const int64_t o = Bt.po[p], len = Bt.po[p + 1] - o;
-    if (!Bt.live[p]) {
-      if (f32) CPM_CUDA(cudaMemsetAsync(Bt.y32 + o, 0, len * sizeof(float), s));
-      else CPM_CUDA(cudaMemsetAsync(out + o, 0, len * sizeof(double), s));
-      continue;
-    }
+    if (!Bt.live[p]) continue;  // its output segment was zeroed when it finished
     if (!Bt.pc[p]) {
-      if (f32) CPM_CUDA(cudaMemcpyAsync(Bt.y32 + o, Bt.x32 + o, len * sizeof(float), cudaMemcpyDeviceToDevice, s));
-      else CPM_CUDA(cudaMemcpyAsync(out + o, x + o, len * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      CPM_CUDA(cudaMemcpyAsync(out + o, x + o, len * sizeof(double), cudaMemcpyDeviceToDevice, sp));
       continue;
     }
-    if (f32) CPM_TRY(oras_run(Bt.pc[p], Bt.x32 + o, Bt.y32 + o, CPM_F32, Bt.nrhs[p], transpose, s));
-    else CPM_TRY(oras_run(Bt.pc[p], x + o, out + o, CPM_F64, Bt.nrhs[p], transpose, s));
+    if (f32) {
+      KL(kb_d2f<<<grid_n(len), 256, 0, sp>>>(x + o, Bt.x32 + o, len));
+      CPM_TRY(oras_run(Bt.pc[p], Bt.x32 + o, Bt.y32 + o, CPM_F32, Bt.nrhs[p], transpose, sp));
+      KL(kb_f2d<<<grid_n(len), 256, 0, sp>>>(Bt.y32 + o, out + o, len));
+    } else {
+      CPM_TRY(oras_run(Bt.pc[p], x + o, out + o, CPM_F64, Bt.nrhs[p], transpose, sp));
+    }
   }
-  if (f32) KL(kb_f2d<<<grid_n(Bt.N), 256, 0, s>>>(Bt.y32, out, Bt.N));
-  return CPM_OK;
+  return Bt.fan_in(s);
 }
 
 // One GMRES(m) cycle for every active system on M d = b (x += P V y), from
@@ -372,7 +421,7 @@ cpm_status batch_cycle(Batch& Bt, double* x, bool f32, int transpose, int maxit,
   const int S = Bt.S, m = Bt.m;
   const int gs = (S + 127) / 128;
   // |r_s|^2, v_0 = r / |r|
-  CPM_TRY(seg_dots(Bt, Bt.r, 1, Bt.r, Bt.X.rr, 1, 0, s));
+  CPM_TRY(seg_dots(Bt, Bt.G, Bt.r, 1, Bt.r, Bt.X.rr, 1, 0, s));
   KL(kb_cycle_init<<<gs, 128, 0, s>>>(S, m, Bt.X, maxit, rtol, inner));
   KL(kb_scale<<<Bt.NB, RED_THREADS, 0, s>>>(Bt.G, Bt.r, Bt.X.scale, Bt.V));
   for (int j = 0; j < m; ++j) {
@@ -383,15 +432,16 @@ cpm_status batch_cycle(Batch& Bt, double* x, bool f32, int transpose, int maxit,
     const int nv = j + 1, cs = chunk_of(nv);
     for (int t0 = 0; t0 < nv; t0 += cs) {
       const int nc = std::min(cs, nv - t0);
-      CPM_TRY(seg_dots(Bt, Bt.V + (int64_t)t0 * Bt.N, nc, Bt.w, Bt.X.hc + t0, m + 2, 0, s));
+      CPM_TRY(seg_dots(Bt, Bt.GA, Bt.V + (int64_t)t0 * Bt.N, nc, Bt.w, Bt.X.hc + t0, m + 2, 0, s));
     }
     for (int t0 = 0; t0 < nv; t0 += cs) {
       const int nc = std::min(cs, nv - t0);
       const bool last = t0 + cs >= nv;
-      CPM_TRY(seg_update(Bt, Bt.V + (int64_t)t0 * Bt.N, nc, Bt.X.hc + t0, m + 2, Bt.w, last, Bt.X.hc + nv, m + 2, s));
+      CPM_TRY(seg_update(Bt, Bt.GA, Bt.V + (int64_t)t0 * Bt.N, nc, Bt.X.hc + t0, m + 2, Bt.w, last, Bt.X.hc + nv,
+                         m + 2, s));
     }
     KL(kb_givens<<<gs, 128, 0, s>>>(S, m, j, Bt.X, maxit));
-    if (j + 1 < m) KL(kb_scale<<<Bt.NB, RED_THREADS, 0, s>>>(Bt.G, Bt.w, Bt.X.scale, Bt.V + (int64_t)(j + 1) * Bt.N));
+    if (j + 1 < m) KL(kb_scale<<<Bt.NB, RED_THREADS, 0, s>>>(Bt.GA, Bt.w, Bt.X.scale, Bt.V + (int64_t)(j + 1) * Bt.N));
     CPM_CUDA(cudaGetLastError());
   }
   // x += P (V y), y per system over its kk columns
@@ -400,7 +450,7 @@ cpm_status batch_cycle(Batch& Bt, double* x, bool f32, int transpose, int maxit,
   const int cs = chunk_of(m);
   for (int t0 = 0; t0 < m; t0 += cs) {
     const int nc = std::min(cs, m - t0);
-    CPM_TRY(seg_update(Bt, Bt.V + (int64_t)t0 * Bt.N, nc, Bt.ny + t0, m, Bt.t, false, nullptr, 0, s));
+    CPM_TRY(seg_update(Bt, Bt.G, Bt.V + (int64_t)t0 * Bt.N, nc, Bt.ny + t0, m, Bt.t, false, nullptr, 0, s));
   }
   CPM_TRY(batch_P(Bt, Bt.t, Bt.z, f32, transpose, s));
   KL(kb_axpy<<<grid_n(Bt.N), 256, 0, s>>>(Bt.z, x, Bt.N));
@@ -438,6 +488,7 @@ cpm_status solve_batch(int nprob, const cpm_band* const* bands, const oras_pc* c
     if (mixed && Bt.pc[p] && Bt.pc[p]->store == CPM_F64)
       return fail(CPM_ERR_ARG, "mixed precision needs FP32 or BF16 factors (problem %d)", p);
   cpm_status st = make_segments(Bt, so, s);
+  if (st == CPM_OK) st = Bt.make_streams();
   auto bail = [&](cpm_status e) {
     Bt.release(s);
     cudaStreamSynchronize(s);
@@ -450,6 +501,9 @@ cpm_status solve_batch(int nprob, const cpm_band* const* bands, const oras_pc* c
     if (e_ != CPM_OK) return bail(e_); \
   } while (0)
   BTRY(Bt.get(&Bt.V, (size_t)(m + 1) * Bt.N, s));
+  // a stopped system's later basis vectors are left as they are (finite: an
+  // older vector or these zeros) and enter the correction with coefficient 0
+  BTRY(cudaMemsetAsync(Bt.V, 0, (size_t)(m + 1) * Bt.N * sizeof(double), s) == cudaSuccess ? CPM_OK : CPM_ERR_CUDA);
   BTRY(Bt.get(&Bt.w, Bt.N, s));
   BTRY(Bt.get(&Bt.z, Bt.N, s));
   BTRY(Bt.get(&Bt.t, Bt.N, s));
@@ -478,7 +532,8 @@ cpm_status solve_batch(int nprob, const cpm_band* const* bands, const oras_pc* c
   if (mixed) BTRY(Bt.get(&d, Bt.N, s));
   BTRY(cudaMemsetAsync(X.its, 0, S * sizeof(int32_t), s) == cudaSuccess ? CPM_OK : CPM_ERR_CUDA);
   // |f_s|
-  BTRY(seg_dots(Bt, f, 1, f, X.rr, 1, 0, s));
+  Bt.GA = Seg{Bt.G.sys, Bt.G.lo, Bt.G.hi, X.active};
+  BTRY(seg_dots(Bt, Bt.G, f, 1, f, X.rr, 1, 0, s));
   std::vector<double> h2(S), fn(S);
   BTRY(cudaMemcpyAsync(h2.data(), X.rr, S * sizeof(double), cudaMemcpyDeviceToHost, s) == cudaSuccess ? CPM_OK
                                                                                                   : CPM_ERR_CUDA);
@@ -497,7 +552,7 @@ cpm_status solve_batch(int nprob, const cpm_band* const* bands, const oras_pc* c
     // true residual of every system (FP64): r = f - M u
     BTRY(batch_M(Bt, u, Bt.r, false, transpose, s, true));
     KL(kb_sub<<<grid_n(Bt.N), 256, 0, s>>>(f, Bt.r, Bt.N));
-    BTRY(seg_dots(Bt, Bt.r, 1, Bt.r, X.rr, 1, 0, s));
+    BTRY(seg_dots(Bt, Bt.G, Bt.r, 1, Bt.r, X.rr, 1, 0, s));
     BTRY(cudaMemcpyAsync(h2.data(), X.rr, S * sizeof(double), cudaMemcpyDeviceToHost, s) == cudaSuccess
              ? CPM_OK
              : CPM_ERR_CUDA);
@@ -517,6 +572,14 @@ cpm_status solve_batch(int nprob, const cpm_band* const* bands, const oras_pc* c
       }
     }
     if (!any) break;
+    Bt.zeroed.resize(nprob, 0);
+    for (int p = 0; p < nprob; ++p)
+      if (!Bt.live[p] && !Bt.zeroed[p]) {
+        const int64_t o = Bt.po[p], len = Bt.po[p + 1] - o;
+        BTRY(cudaMemsetAsync(Bt.z + o, 0, len * sizeof(double), s) == cudaSuccess ? CPM_OK : CPM_ERR_CUDA);
+        BTRY(cudaMemsetAsync(Bt.w + o, 0, len * sizeof(double), s) == cudaSuccess ? CPM_OK : CPM_ERR_CUDA);
+        Bt.zeroed[p] = 1;
+      }
     ++cycles;
     if (!mixed) {
       BTRY(batch_cycle(Bt, u, false, transpose, prm->maxit, prm->rtol, 0, s));
