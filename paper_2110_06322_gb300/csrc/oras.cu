@@ -89,12 +89,12 @@ __global__ void __launch_bounds__(ASM_WARPS * 32)
       const int32_t* b = A.rbase + 3 * (int64_t)r;
       const int32_t q0 = bm_rank_known(A.amap, A.g, b[0] + u, b[1] + v, b[2]);
       const double* w = A.w1d + (int64_t)r * 3 * P1;
-      const double wuv = dm(w[u], w[P1 + v]);
+      const double wuv = mptr ? dm(w[u], w[P1 + v]) : 0.0;  // the counting pass needs columns only
 #pragma unroll
       for (int t = 0; t < P1; ++t) {
         const int pos = n * NC + uv * P1 + t;
         lcol[pos] = q0 + t;
-        lterm[pos] = dm(A.coef, dm(wuv, w[2 * P1 + t]));
+        if (mptr) lterm[pos] = dm(A.coef, dm(wuv, w[2 * P1 + t]));
       }
     }
     if (lane == 0) {  // diagonal marker, last in list order
@@ -589,6 +589,61 @@ __global__ void k_levels(int np, const int64_t* __restrict__ sptr, const int64_t
   if (lane == 0) nlev[j] = mx;
 }
 
+// The same with the subdomain's levels in shared memory (16-bit: a level is
+// at most the row count, below 2^15 here) and the next row's bounds and
+// columns loaded while the current row is reduced: one warp per subdomain,
+// one warp per block, so many subdomains share an SM.
+constexpr int LEV_PF = 3;  // dependency columns per lane fetched a row ahead
+__global__ void __launch_bounds__(32)
+    k_levels_smem(const int64_t* __restrict__ sptr, const int64_t* __restrict__ rptr,
+                  const int32_t* __restrict__ col, const int32_t* __restrict__ dpos, int lower, int32_t* lev,
+                  int32_t* nlev) {
+  extern __shared__ int16_t slev[];
+  const int lane = threadIdx.x;
+  const int j = blockIdx.x;
+  const int64_t base = sptr[j], n = sptr[j + 1] - base;
+  auto bounds = [&](int64_t t, int64_t& e0, int64_t& e1) {
+    const int64_t q = base + (lower ? t : n - 1 - t);
+    e0 = lower ? rptr[q] : rptr[q] + dpos[q] + 1;
+    e1 = lower ? rptr[q] + dpos[q] : rptr[q + 1];
+  };
+  int64_t e0 = 0, e1 = 0;
+  int32_t c[LEV_PF];
+  if (n > 0) {
+    bounds(0, e0, e1);
+#pragma unroll
+    for (int k = 0; k < LEV_PF; ++k) c[k] = e0 + lane + 32 * k < e1 ? col[e0 + lane + 32 * k] : -1;
+  }
+  int32_t mx = 0;
+  for (int64_t t = 0; t < n; ++t) {
+    int64_t f0 = 0, f1 = 0;
+    int32_t cn[LEV_PF];
+    if (t + 1 < n) {
+      bounds(t + 1, f0, f1);
+#pragma unroll
+      for (int k = 0; k < LEV_PF; ++k) cn[k] = f0 + lane + 32 * k < f1 ? col[f0 + lane + 32 * k] : -1;
+    }
+    int32_t l = 0;
+#pragma unroll
+    for (int k = 0; k < LEV_PF; ++k)
+      if (c[k] >= 0) l = max(l, (int32_t)slev[c[k]]);
+    for (int64_t e = e0 + lane + 32 * LEV_PF; e < e1; e += 32) l = max(l, (int32_t)slev[col[e]]);
+    for (int o = 16; o > 0; o >>= 1) l = max(l, __shfl_xor_sync(FULL, l, o));
+    const int64_t tl = lower ? t : n - 1 - t;
+    if (lane == 0) {
+      slev[tl] = (int16_t)(l + 1);
+      lev[base + tl] = l + 1;
+    }
+    mx = max(mx, l + 1);
+    __syncwarp();
+    e0 = f0;
+    e1 = f1;
+#pragma unroll
+    for (int k = 0; k < LEV_PF; ++k) c[k] = cn[k];
+  }
+  if (lane == 0) nlev[j] = mx;
+}
+
 __global__ void k_level_count(int64_t nloc, const int32_t* __restrict__ lsub, const int32_t* __restrict__ lvsub,
                               const int32_t* __restrict__ lev, int32_t* lcnt) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nloc; q += (int64_t)gridDim.x * blockDim.x)
@@ -775,7 +830,13 @@ cpm_status build_schedule(oras_pc* P, const int64_t* rptr, const int32_t* col, c
   int32_t *lev = nullptr, *nlev = nullptr;
   CPM_TRY(dalloc(&lev, nloc, s));
   CPM_TRY(dalloc(&nlev, np, s));
-  KL(k_levels<<<(np + 3) / 4, 128, 0, s>>>(np, P->sptr, rptr, col, dpos, lower, lev, nlev));
+  if (P->max_rows < 32768 && P->max_rows * (int64_t)sizeof(int16_t) <= 200 * 1024) {
+    const int sm = (int)std::max<int64_t>(P->max_rows * (int64_t)sizeof(int16_t), 16);
+    CPM_CUDA(cudaFuncSetAttribute(k_levels_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    KL(k_levels_smem<<<np, 32, sm, s>>>(P->sptr, rptr, col, dpos, lower, lev, nlev));
+  } else {
+    KL(k_levels<<<(np + 3) / 4, 128, 0, s>>>(np, P->sptr, rptr, col, dpos, lower, lev, nlev));
+  }
   CPM_CUDA(cudaGetLastError());
   std::vector<int32_t> hn(np);
   CPM_CUDA(cudaMemcpyAsync(hn.data(), nlev, np * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
