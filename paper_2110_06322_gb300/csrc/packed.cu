@@ -14,8 +14,9 @@
 // sizes (in 16-byte units) lets the copying thread walk them without reading
 // global metadata on the critical path.
 //
-// The apply runs one CTA per subdomain: thread 0 streams the chunk sequence
-// (forward then backward) into a ring of NSTAGE shared-memory buffers with
+// The apply runs one CTA per subdomain: one lane of a producer warp streams
+// the chunk sequence (forward then backward) into a ring of NSTAGE
+// shared-memory buffers with
 // cp.async.bulk (the 1-D TMA copy) and mbarrier transaction counts, NSTAGE-1
 // chunks ahead; all warps consume the current chunk from shared memory
 // (SW_LPR lanes per row: gather the local vector, multiply, shuffle-reduce;
