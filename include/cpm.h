@@ -25,9 +25,9 @@
  *   - Working memory comes stream-ordered from the device's default memory
  *     pool (cudaMallocAsync).  On its first allocation on a device the library
  *     raises that pool's release threshold to 64 GiB, so that memory freed by
- *     one solve or set-up is reused by the next instead of being returned to
- *     the driver at every synchronisation; cudaMemPoolTrimTo on the default
- *     pool gives it back.
+ *     one solve or set-up is reused by the next instead of being unmapped at
+ *     every synchronisation; cudaMemPoolTrimTo on the default pool gives it
+ *     back.
  *   - Errors are returned as cpm_status codes; a message for the last error
  *     of the calling thread is available from cpm_last_error().  No call
  *     aborts the process or traps the device.  Kernels that wait on a
