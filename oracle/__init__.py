@@ -83,6 +83,7 @@ def lib():
         "orc_oras_sub_size": (i64, [vp, i32]),
         "orc_oras_sub_nodes": (None, [vp, i32, _i32p]),
         "orc_oras_sub_matrix": (vp, [vp, i32]),
+        "orc_oras_depth": (i32, [vp, i32, i32]),
         "orc_oras_sub_matrix_unfactored": (vp, [vp, vp, vp, i32]),
         "orc_oras_apply": (None, [vp, _f64p, _f64p, i32]),
         "orc_gmres": (i32, [vp, vp, i32, _f64p, _f64p, i32, i32, f64, i32, pi32, pf64]),
@@ -235,7 +236,7 @@ class BandError(RuntimeError):
 class ORAS:
     """(O)RAS preconditioner (Section 2.2) over an oracle band and matrix."""
 
-    LOCAL_CANONICAL, LOCAL_DISTANCE = 0, 1
+    LOCAL_CANONICAL, LOCAL_DISTANCE, LOCAL_SHELLS = 0, 1, 2
 
     def __init__(self, band, M, nparts, overlap, robin=False, alpha=4.0, alpha_cross=20.0, exact=False,
                  order=LOCAL_DISTANCE):
@@ -266,6 +267,11 @@ class ORAS:
 
     def sub_factors(self, j):
         return CSR(lib().orc_oras_sub_matrix(self._p, j))
+
+    def depth(self, j, lower=True):
+        """Number of dependency levels of subdomain j's lower (or upper)
+        triangular sweep in its local order."""
+        return int(lib().orc_oras_depth(self._p, int(j), int(bool(lower))))
 
     def sub_matrix(self, j):
         return CSR(lib().orc_oras_sub_matrix_unfactored(self.band._p, self.M._p, self._p, j))
