@@ -667,9 +667,10 @@ int oras_setup(const Band& B, const CSR& M, ORAS& P) {
       // first (shell = floor(dist / h)); inside a shell the 8 colours of the
       // lattice parity (i mod 2, j mod 2, k mod 2), colour 0 first; inside a
       // colour, canonical.  Measured on the torus against the plain
-      // descending-distance order: triangular sweeps 14 / 25 / 49 % shallower
-      // and GMRES to 1e-8 in 19 / 23 / 24 % fewer iterations at h = 0.025 (16
-      // parts), 0.0125 (64) and 0.00625 (256).
+      // descending-distance order: triangular sweeps 14 / 25 / 49 / 56 %
+      // shallower at h = 0.025 (16 parts), 0.0125 (64), 0.00625 (256) and
+      // 0.004 (512), and GMRES to 1e-8 in 19 / 23 / 24 % fewer iterations on
+      // the first three.
       std::vector<int64_t> shell(mem.size());
       std::vector<int> colour(mem.size());
       for (size_t q = 0; q < mem.size(); ++q) {
