@@ -149,11 +149,16 @@ typedef struct {
   double alpha;
   double alpha_cross;
   int32_t store;
+  int32_t order;  /* local order of the ILU(0) factorisation: 1 descending distance
+                     to the surface; 2 distance shells of width h (outermost
+                     first), then lattice-parity colours; ties canonical */
 } oras_params;
 
 /* oras_setup -- partition, overlap growth, local matrices A_j = R_j M R_j^T
- * (+ Robin term), and ILU(0) of each A_j in its local order (descending
- * distance to the surface, ties by canonical index).  c is the shift of M. */
+ * (+ Robin term), and ILU(0) of each A_j in its local order (prm->order: 1
+ * descending distance to the surface, ties by canonical index; 2 distance
+ * shells of width h, then lattice-parity colours).  c is the shift of M.
+ * The paper leaves the local order to PETSc (Section 4.1.1). */
 cpm_status oras_setup(const cpm_band* band, const oras_params* prm, double c, void* stream, oras_pc** out);
 
 /* oras_apply -- z = sum_j Rtilde_j^T (L_j U_j)^{-1} R_j r (transpose = 0) or

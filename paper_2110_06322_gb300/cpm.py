@@ -33,7 +33,7 @@ class cpm_surface(C.Structure):
 
 class oras_params(C.Structure):
     _fields_ = [("nparts", C.c_int32), ("overlap", C.c_int32), ("robin", C.c_int32), ("alpha", C.c_double),
-                ("alpha_cross", C.c_double), ("store", C.c_int32)]
+                ("alpha_cross", C.c_double), ("store", C.c_int32), ("order", C.c_int32)]
 
 
 class cpm_solve_params(C.Structure):
@@ -177,8 +177,10 @@ def cpm_dot(band, a, b, out, stream=None):
     return out
 
 
-def oras_setup(band, c, nparts, overlap, robin=False, alpha=4.0, alpha_cross=20.0, store=CPM_F32, stream=None):
-    prm = oras_params(int(nparts), int(overlap), int(bool(robin)), float(alpha), float(alpha_cross), int(store))
+def oras_setup(band, c, nparts, overlap, robin=False, alpha=4.0, alpha_cross=20.0, store=CPM_F32, order=1,
+               stream=None):
+    prm = oras_params(int(nparts), int(overlap), int(bool(robin)), float(alpha), float(alpha_cross), int(store),
+                      int(order))
     out = C.c_void_p()
     _check(lib().oras_setup(band, C.byref(prm), float(c), _stream(stream), C.byref(out)))
     return out
@@ -292,11 +294,11 @@ class Band:
 class Schwarz:
     """(O)RAS preconditioner over a Band (Section 2.2)."""
 
-    def __init__(self, band, c, nparts, overlap, robin=False, alpha=4.0, alpha_cross=20.0, store=CPM_F32,
+    def __init__(self, band, c, nparts, overlap, robin=False, alpha=4.0, alpha_cross=20.0, store=CPM_F32, order=1,
                  stream=None):
         self.band = band
         self.c = float(c)
-        self.handle = oras_setup(band.handle, c, nparts, overlap, robin, alpha, alpha_cross, store, stream)
+        self.handle = oras_setup(band.handle, c, nparts, overlap, robin, alpha, alpha_cross, store, order, stream)
         npt, rows, nnz, lev = C.c_int32(), C.c_int64(), C.c_int64(), C.c_int32()
         _check(lib().oras_info(self.handle, C.byref(npt), C.byref(rows), C.byref(nnz), C.byref(lev)))
         self.nparts, self.total_rows, self.total_nnz, self.max_levels = npt.value, rows.value, nnz.value, lev.value

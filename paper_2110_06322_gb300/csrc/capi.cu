@@ -104,6 +104,7 @@ cpm_status oras_setup(const cpm_band* band, const oras_params* prm, double c, vo
     return fail(CPM_ERR_ARG, "Robin parameters must be >= 0 (infinity allowed)");
   if (prm->store != CPM_F32 && prm->store != CPM_BF16 && prm->store != CPM_F64)
     return fail(CPM_ERR_ARG, "store must be CPM_F64, CPM_F32 or CPM_BF16");
+  if (prm->order != 1 && prm->order != 2) return fail(CPM_ERR_ARG, "order must be 1 (distance) or 2 (shells)");
   if (!std::isfinite(c)) return fail(CPM_ERR_NAN, "shift c is not finite");
   g_err[0] = 0;
   return oras_build(band, prm, c, as_stream(stream), out);

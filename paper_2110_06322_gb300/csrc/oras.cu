@@ -374,7 +374,12 @@ __global__ void k_sub_fill(int64_t nA, const int32_t* __restrict__ memb, const i
 
 // sort keys: descending distance (bit pattern of a non-negative double is
 // monotone), then ascending canonical index
-__global__ void k_sort_prep(SurfDev S, double h, const int32_t* __restrict__ ijkA, int np,
+// Sort keys of the local order (ascending key, ties by canonical index):
+// order 1: descending distance to the surface;
+// order 2: distance shells of width h, outermost first (shell = floor(dist / h),
+//          correctly rounded division as in the oracle), then the 8 colours of
+//          the lattice parity (i mod 2, j mod 2, k mod 2).
+__global__ void k_sort_prep(SurfDev S, double h, int order, const int32_t* __restrict__ ijkA, int np,
                             const int64_t* __restrict__ sptr, const int64_t* __restrict__ poff,
                             const int32_t* __restrict__ snode, unsigned long long* key, int32_t* val) {
   const int j = blockIdx.x;
@@ -384,7 +389,13 @@ __global__ void k_sort_prep(SurfDev S, double h, const int32_t* __restrict__ ijk
       const int32_t q = snode[sptr[j] + t];
       const double d = surf_dist(S, dm((double)ijkA[3 * q], h), dm((double)ijkA[3 * q + 1], h),
                                  dm((double)ijkA[3 * q + 2], h));
-      key[poff[j] + t] = ~(unsigned long long)__double_as_longlong(d);
+      if (order == 2) {
+        const unsigned long long shell = (unsigned long long)floor(ddv(d, h));
+        const unsigned colour = (unsigned)((ijkA[3 * q] & 1) | ((ijkA[3 * q + 1] & 1) << 1) | ((ijkA[3 * q + 2] & 1) << 2));
+        key[poff[j] + t] = ((0xFFFFFFFFull - shell) << 3) | colour;
+      } else {
+        key[poff[j] + t] = ~(unsigned long long)__double_as_longlong(d);
+      }
       val[poff[j] + t] = q;
     } else {
       key[poff[j] + t] = ~0ull;
@@ -910,6 +921,7 @@ cpm_status oras_build(const cpm_band* B, const oras_params* prm, double c, cudaS
   P->np = prm->nparts;
   P->overlap = prm->overlap;
   P->robin = prm->robin;
+  P->order = prm->order;
   P->alpha = prm->alpha;
   P->alpha_x = prm->alpha_cross;
   P->store = prm->store;
@@ -1024,7 +1036,7 @@ cpm_status oras_build(const cpm_band* B, const oras_params* prm, double c, cudaS
     for (int d = 0; d < 3; ++d) S.c[d] = B->surf.param[d];
     S.a = B->surf.param[3];
     S.b = B->surf.kind == 1 ? B->surf.param[4] : 0.0;
-    KL(k_sort_prep<<<np, 256, 0, s>>>(S, B->h, B->ijkA, np, P->sptr, poff, P->snode, skey, sval));
+    KL(k_sort_prep<<<np, 256, 0, s>>>(S, B->h, P->order, B->ijkA, np, P->sptr, poff, P->snode, skey, sval));
   }
   KL(k_bitonic_sub<<<np, 1024, 0, s>>>(poff, skey, sval));
   TRY(dalloc(&P->owned, nloc, s));

@@ -31,6 +31,7 @@ struct oras_pc {
   const cpm_band* band = nullptr;
   int device = 0;
   int np = 0, overlap = 0, robin = 0, store = CPM_F32;
+  int order = 1;  // local order of the factorisation: 1 distance, 2 shells + lattice colours
   double alpha = 0, alpha_x = 0, c = 0;
   int64_t nA = 0;
   int32_t* part = nullptr;    // [nA] disjoint part of each active node

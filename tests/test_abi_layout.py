@@ -12,7 +12,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 STRUCTS = {
     "cpm_surface": ["kind", "param"],
-    "oras_params": ["nparts", "overlap", "robin", "alpha", "alpha_cross", "store"],
+    "oras_params": ["nparts", "overlap", "robin", "alpha", "alpha_cross", "store", "order"],
     "cpm_solve_params": ["restart", "maxit", "rtol", "mixed", "reorth", "inner_rtol", "timing"],
     "cpm_solve_info": ["iters", "restarts", "ir_steps", "rel_residual", "status", "ms_precond", "ms_operator",
                        "n_precond", "n_operator"],
