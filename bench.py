@@ -1,24 +1,42 @@
 #!/usr/bin/env python
 """Benchmark of the GB300 ORAS-GMRES closest point method solver.
 
-One step = the whole hot path on one synthetic problem, the shifted surface
-Poisson problem (c - Delta_S) u = f (arXiv 2110.06322, eq. shiftPoisson) on a
-torus R = 1, r = 0.4 at h = 0.004 (about 5.7M band points, tricubic
-interpolation), c = 10, f = 20 random Fourier modes in the torus angles:
+Headline (default, --workload torus_h0.002): the shifted surface Poisson
+problem (c - Delta_S) u = f (arXiv 2110.06322, eq. shiftPoisson) on a torus
+R = 1, r = 0.4 at h = 0.002 (about 22.8M band points, tricubic interpolation),
+c = 10, f = 20 random Fourier modes in the torus angles.  One step is
 
   band build (Sigma_A, Sigma_G, E rows)  ->  Schwarz set-up (512 parts,
-  overlap 2, ILU(0))  ->  mixed-precision solve M u = f  ->  mixed-precision
-  adjoint solve M^T lambda = g, both to relative residual 1e-8.
+  overlap 2, ILU(0))  ->  mixed-precision solve M u = f (FP32 operator and
+  Schwarz applies inside FP64 iterative refinement) to the relative residual
+  that keeps the error within 1e-8 of the FP64 solution.
 
-Reported value: band-point iterations per second of the whole step, N_A times
-the GMRES iterations of both solves (inner iterations of the refinement
-included) divided by the step time.  Also reported: solves/s, and one plain
-FP64 solve of the same system for comparison.
+Reported value: band-point iterations per second of the whole step (N_A times
+the GMRES iterations divided by the step time), with inputs resident in HBM;
+`solves_per_s` beside it.  Outside the timed region: the plain FP64 GPU solve
+of the same system (speed-up and iterations), an FP64 reference solution at a
+tight tolerance (the stated errors of both solutions), the BF16 factor-storage
+ablation, the sphere case h = 0.1 (microseconds per iteration), the forward +
+adjoint pipeline at h = 0.004, end to end through host buffers, the roofline of
+the dominant kernel from a separately instrumented solve, and the FP64 CPU
+oracle on a bounded sample of the same workload on one core and on all cores.
+
+Other modes:
+  --workload torus_h0.004   the same line at h = 0.004 (5.7M points)
+  --workload batch          many uneven problems in one cpm_solve_batch call
+                            against the same systems solved one by one
+  --workload schnakenberg   differentiable Schnakenberg run (eq. schnack): forward
+                            steps and the checkpointed adjoint gradient
+  --profile KIND            a bare loop for ncu (no clocks, no oracle): `op`, `opT`
+                            or `pc` (one FP32 apply per step), `setup` (band,
+                            Schwarz set-up and first transposed applies per step),
+                            `pipeline` (band, set-up, mixed forward + adjoint solve,
+                            capped by --maxit)
 
 --impl reference times the FP64 CPU oracle (oracle/) on the host cores, each
 step a bounded sample of the same workload (the same torus at h = 0.025 with
-16 parts, so that each subdomain has about as many rows as in the GPU
-workload), in the same unit.
+16 parts, so each subdomain has about as many rows as in the GPU workload), in
+the same unit.
 
 Multi-GPU: the problems are independent, so N ranks run N replicas with no
 collective on the data path ("scaling": "weak"); value = all ranks' band-point
@@ -28,6 +46,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -39,18 +58,15 @@ sys.path.insert(0, ROOT)
 
 from paper_2110_06322_gb300 import inputs  # noqa: E402
 
-WORKLOAD = "torus_h0.004"
+WORKLOAD = "torus_h0.002"
 SAMPLE = dict(h=0.025, nparts=16)  # oracle sample: same torus, same subdomain size
-# DRAM bytes per stored factor entry of one FP32 Schwarz apply (dram__bytes_read.sum + dram__bytes_write.sum
-# of one ncu capture on the torus h = 0.0125 / 64-part case, 564.35 MB over 88,019,898 entries; summary in
-# profiles/k_schwarz_pk_fp32_torus_h0.0125.md).  Traffic grows with the stored entries, so a full launch moves
-# this times Sigma nnz(A_j).  Re-measure when k_schwarz_pk changes.
-SCHWARZ_TRAFFIC_PER_ENTRY = 564.354048e6 / 88019898
-METRIC = "ORAS-GMRES band-pt*iters/s (full pipeline: band, set-up, mixed forward + adjoint solve at 1e-8)"
+METRIC = "ORAS-GMRES band-pt*iters/s (band, set-up and mixed-precision solve to error 1e-8 of FP64)"
 UNIT = "band-pt*iters/s"
+REF_RTOL = 1e-11   # FP64 reference solution: far below the 1e-8 error statement
+E2E_STEPS = 3      # end-to-end steps (host buffers): at most this many
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -58,12 +74,20 @@ def parse():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    return ap.parse_args()
+    ap.add_argument("--quick", action="store_true", help="headline only: skip the measurements beside it")
+    ap.add_argument("--profile", choices=["op", "opT", "pc", "setup", "pipeline"], default=None)
+    ap.add_argument("--maxit", type=int, default=50000, help="--profile pipeline: iteration cap of each solve")
+    ap.add_argument("--problems", type=int, default=96, help="--workload batch: number of problems")
+    ap.add_argument("--hs", default="0.05,0.025,0.0125,0.00625", help="--workload batch: grid spacings")
+    ap.add_argument("--fd-steps", type=int, default=0,
+                    help="--workload schnakenberg: also check dL/dD_u, dL/dD_v of a run of this many steps "
+                         "against central differences (solves at --rtol)")
+    ap.add_argument("--rtol", type=float, default=None, help="--workload schnakenberg: solve tolerance")
+    return ap.parse_args(argv)
 
 
 def workload(name):
-    w = dict(inputs.WORKLOADS[name])
-    return w
+    return dict(inputs.WORKLOADS[name])
 
 
 def rhs_pair(cp, w):
@@ -136,56 +160,161 @@ def reduce_over_ranks(ms, iters, device="cpu"):
 
 # ---------------------------------------------------------------- oracle sample (CPU)
 def oracle_step(w, h, nparts):
-    """One full pipeline of the FP64 oracle on the sample; returns (seconds,
-    band-point iterations, solves)."""
+    """One step of the FP64 oracle on the sample (band, M, Schwarz set-up,
+    forward GMRES); returns (seconds, band-point iterations, band points)."""
     import oracle
     t0 = time.perf_counter()
     B = oracle.Band(w["kind"], w["params"], h, w["p"])
     M = B.M(w["c"])
     cp = B.export()[3][: B.n_active]
-    f, g = rhs_pair(cp, w)
+    f, _ = rhs_pair(cp, w)
     P = oracle.ORAS(B, M, nparts, w["overlap"], robin=w["robin"], alpha=w.get("alpha", 4.0),
-                    alpha_cross=w.get("alpha_cross", 20.0))
+                    alpha_cross=w.get("alpha_cross", 20.0), order=w.get("order", 1))
     u, i1 = oracle.gmres(M, f, P, restart=w["restart"], rtol=w["rtol"], maxit=20000)
-    lam, i2 = oracle.gmres(M.transpose(), g, P, transpose=True, restart=w["restart"], rtol=w["rtol"], maxit=20000)
     dt = time.perf_counter() - t0
-    return dt, B.n_active * (i1["iters"] + i2["iters"]), 2, B.n_active
+    return dt, B.n_active * i1["iters"], B.n_active
 
 
-def cpu_baseline(w):
-    dt, bpi, solves, n = oracle_step(w, SAMPLE["h"], SAMPLE["nparts"])
-    return {"value": bpi / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"oracle (FP64, single thread) full pipeline on the same torus at h={SAMPLE['h']} "
-                      f"({n} band points, {SAMPLE['nparts']} parts, overlap {w['overlap']}): band, M, "
-                      f"ILU(0) set-up, forward + adjoint GMRES to {w['rtol']:g}; {dt:.1f} s"}
+def _oracle_worker(args):
+    name, h, nparts = args
+    return oracle_step(workload(name), h, nparts)
+
+
+def host_cores():
+    try:
+        aff = len(os.sched_getaffinity(0))
+    except AttributeError:
+        aff = os.cpu_count() or 1
+    return os.cpu_count() or 1, aff
+
+
+def cpu_baseline(name):
+    """The oracle as it stands on the sample: one step on one core, and one
+    step per core on all cores at once (independent processes; aggregate
+    throughput = all work / wall time)."""
+    import multiprocessing as mp
+    w = workload(name)
+    dt, bpi, n = oracle_step(w, SAMPLE["h"], SAMPLE["nparts"])
+    nproc, aff = host_cores()
+    one = {"value": bpi / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"oracle (FP64, single thread) on the same torus at h={SAMPLE['h']} ({n} band points, "
+                     f"{SAMPLE['nparts']} parts, overlap {w['overlap']}): band, M, ILU(0) set-up, forward GMRES "
+                     f"to {w['rtol']:g}; {dt:.1f} s; host nproc {nproc}, affinity {aff}"}
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(aff) as pool:
+        res = pool.map(_oracle_worker, [(name, SAMPLE["h"], SAMPLE["nparts"])] * aff)
+    wall = time.perf_counter() - t0
+    allc = {"value": sum(r[1] for r in res) / wall, "unit": UNIT, "cores": aff, "kind": "oracle",
+            "sample": f"{aff} copies of the single-thread sample step run at once, one per core "
+                      f"({wall:.1f} s wall, process start-up included)"}
+    return one, allc
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    w = workload(args.workload)
+    name = args.workload if args.workload in inputs.WORKLOADS else WORKLOAD
+    w = workload(name)
     for _ in range(args.warmup):
         oracle_step(w, SAMPLE["h"], SAMPLE["nparts"])
-    tot_t, tot_bpi, tot_solves = 0.0, 0, 0
+    tot_t, tot_bpi = 0.0, 0
+    n = 0
     for _ in range(args.steps):
-        dt, bpi, solves, n = oracle_step(w, SAMPLE["h"], SAMPLE["nparts"])
+        dt, bpi, n = oracle_step(w, SAMPLE["h"], SAMPLE["nparts"])
         tot_t += dt
         tot_bpi += bpi
-        tot_solves += solves
     value = tot_bpi / tot_t
+    nproc, aff = host_cores()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{args.workload} (oracle sample h={SAMPLE['h']}, {SAMPLE['nparts']} parts)"},
+            "config": {"workload": f"{name} (oracle sample h={SAMPLE['h']}, {SAMPLE['nparts']} parts)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"each step: oracle full pipeline on the torus at h={SAMPLE['h']} "
-                                       f"({n} band points)"},
+                             "sample": f"each step: oracle band, set-up and forward solve on the torus at "
+                                       f"h={SAMPLE['h']} ({n} band points); host nproc {nproc}, affinity {aff}"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-# ---------------------------------------------------------------- GPU arm
+# ---------------------------------------------------------------- GPU helpers
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return {}
+
+
+def _events(torch, stream):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def _timed(torch, fn):
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = fn()
+    torch.cuda.synchronize()
+    return out, time.perf_counter() - t0
+
+
+def _rel(torch, a, b):
+    return float(((a - b).norm() / b.norm()).item())
+
+
+def schwarz_for(cpm, B, w, store):
+    return cpm.Schwarz(B, w["c"], w["nparts"], w["overlap"], robin=w["robin"], alpha=w.get("alpha", 4.0),
+                       alpha_cross=w.get("alpha_cross", 20.0), store=store, order=w.get("order", 1))
+
+
+def sphere_case(torch, cpm):
+    """Sphere h = 0.1 (7,508 band points, 8 parts, FP64, rtol 1e-10): the
+    vectors fit in L2, so the case is latency-bound; microseconds per GMRES
+    iteration and solves per second over repeated solves."""
+    w = workload("sphere_h0.1")
+    B = cpm.Band(w["kind"], w["params"], w["h"], w["p"])
+    cp = B.export()[3][: B.n_active].cpu().numpy()
+    f = torch.from_numpy((w["c"] + 12.0) * inputs.y32(cp)).cuda()
+    P = schwarz_for(cpm, B, w, cpm.CPM_F32)
+    kw = dict(restart=w["restart"], rtol=w["rtol"], maxit=5000)
+    cpm.solve(B, f, P, **kw)
+    reps, iters = 20, 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        u, info = cpm.solve(B, f, P, **kw)
+        iters += info["iters"]
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return {"n_active": B.n_active, "iters_per_solve": iters / reps, "us_per_iter": 1e6 * dt / iters,
+            "solves_per_s": reps / dt, "rel_residual": info["rel_residual"]}
+
+
+def pipeline_h004(torch, cpm):
+    """Forward and adjoint mixed-precision solves at h = 0.004 (the transposed
+    operator and Schwarz applies, row A7) after band and set-up."""
+    w = workload("torus_h0.004")
+    B0 = cpm.Band(w["kind"], w["params"], w["h"], w["p"])
+    cp = B0.export()[3][: B0.n_active].cpu().numpy()
+    del B0
+    f_h, g_h = rhs_pair(cp, w)
+    f, g = torch.from_numpy(f_h).cuda(), torch.from_numpy(g_h).cuda()
+    kw = dict(restart=w["restart"], rtol=w["rtol"], maxit=50000, mixed=True)
+
+    def one():
+        B = cpm.Band(w["kind"], w["params"], w["h"], w["p"])
+        P = schwarz_for(cpm, B, w, cpm.CPM_F32)
+        u, i1 = cpm.solve(B, f, P, **kw)
+        lam, i2 = cpm.solve(B, g, P, adjoint=True, **kw)
+        return B.n_active, i1, i2
+    one()
+    (n, i1, i2), dt = _timed(torch, one)
+    return {"n_active": n, "step_s": dt, "forward_iters": i1["iters"], "adjoint_iters": i2["iters"],
+            "band_pt_iters_per_s": n * (i1["iters"] + i2["iters"]) / dt,
+            "forward_rel_residual": i1["rel_residual"], "adjoint_rel_residual": i2["rel_residual"]}
+
+
+# ---------------------------------------------------------------- GPU arm: headline
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -199,39 +328,31 @@ def run_gpu(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     w = workload(args.workload)
-    kind, prm, h, c = w["kind"], w["params"], w["h"], w["c"]
-    robin = w["robin"]
-    alpha, alpha_x = w.get("alpha", 4.0), w.get("alpha_cross", 20.0)
+    kind, prm, h = w["kind"], w["params"], w["h"]
     stream = torch.cuda.current_stream()
 
-    # inputs: the right-hand sides at the closest points (host, once), resident in HBM
+    # inputs: the right-hand side at the closest points (host, once), resident in HBM
     B0 = cpm.Band(kind, prm, h, w["p"])
     n = B0.n_active
     cp = B0.export()[3][:n].cpu().numpy()
-    f_h, g_h = rhs_pair(cp, w)
+    f_h, _ = rhs_pair(cp, w)
     del B0
     f = torch.from_numpy(f_h).cuda()
-    g = torch.from_numpy(g_h).cuda()
     fh_pin = torch.from_numpy(f_h).pin_memory()
-    gh_pin = torch.from_numpy(g_h).pin_memory()
     uh_pin = torch.empty(n, dtype=torch.float64).pin_memory()
-    lh_pin = torch.empty(n, dtype=torch.float64).pin_memory()
-    kw = dict(restart=w["restart"], rtol=w["rtol"], maxit=50000, mixed=True, inner_rtol=1e-4, reorth=0)
+    rtol = w["solve_rtol"]
+    kw = dict(restart=w["restart"], rtol=rtol, maxit=50000, mixed=True, inner_rtol=1e-4, reorth=0)
 
-    def step(fd, gd, timing=False):
+    def step(fd, timing=False, keep=False):
         B = cpm.Band(kind, prm, h, w["p"])
-        P = cpm.Schwarz(B, c, w["nparts"], w["overlap"], robin=robin, alpha=alpha, alpha_cross=alpha_x,
-                        store=cpm.CPM_F32)
-        u, i1 = cpm.solve(B, fd, P, timing=timing, **kw)
-        lam, i2 = cpm.solve(B, gd, P, adjoint=True, timing=timing, **kw)
-        if i1["status"] != 0 or i2["status"] != 0:
-            raise RuntimeError(f"solve did not converge: {i1} {i2}")
-        info = (i1, i2, P.total_nnz, P.total_rows)
-        del P, B
-        return u, lam, info
+        P = schwarz_for(cpm, B, w, cpm.CPM_F32)
+        u, info = cpm.solve(B, fd, P, timing=timing, **kw)
+        if info["status"] != 0:
+            raise RuntimeError(f"solve did not converge: {info}")
+        return u, info, ((B, P) if keep else None)
 
     for _ in range(args.warmup):
-        step(f, g)
+        step(f)
     torch.cuda.synchronize()
 
     def barrier():
@@ -239,102 +360,342 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    # ---- timed region: inputs resident in HBM
+    # ---- timed region: inputs resident in HBM, nothing instrumented
     L0 = cpm.cpm_kernel_launches()
     iters = 0
-    prec_ms, prec_n, nnz, nloc = 0.0, 0, 0, 0
     with Clocks(local) as clk:
         barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0, e1 = _events(torch, stream)
         e0.record(stream)
         for _ in range(args.steps):
-            u, lam, (i1, i2, nnz, nloc) = step(f, g, timing=True)
-            iters += i1["iters"] + i2["iters"]
-            prec_ms += i1["ms_precond"]  # forward solve: FP32 Schwarz applies
-            prec_n += i1["n_precond"]
+            u, info, _ = step(f)
+            iters += info["iters"]
         e1.record(stream)
         barrier()
     launches = cpm.cpm_kernel_launches() - L0
     ms, all_iters = reduce_over_ranks(e0.elapsed_time(e1), iters, device="cuda")
     value = n * all_iters / (ms / 1000.0)
-    solves_per_s = 2 * args.steps * world / (ms / 1000.0)
+    solves_per_s = args.steps * world / (ms / 1000.0)
 
-    # ---- end to end: host buffers in, host buffers out, copies timed
+    # ---- end to end: host buffer in, host buffer out, copies timed
+    e_steps = min(args.steps, E2E_STEPS)
     barrier()
     t0 = time.perf_counter()
     e_iters = 0
-    for _ in range(args.steps):
+    for _ in range(e_steps):
         fd = fh_pin.to("cuda", non_blocking=True)
-        gd = gh_pin.to("cuda", non_blocking=True)
-        u, lam, (i1, i2, _, _) = step(fd, gd)
+        u, info, _ = step(fd)
         uh_pin.copy_(u, non_blocking=True)
-        lh_pin.copy_(lam, non_blocking=True)
-        e_iters += i1["iters"] + i2["iters"]
+        e_iters += info["iters"]
     torch.cuda.synchronize()
     e2e_s, e_all = reduce_over_ranks(time.perf_counter() - t0, e_iters, device="cuda")
     e2e_value = n * e_all / e2e_s
 
-    # ---- plain FP64 solve of the same system (context: mixed vs FP64)
-    B = cpm.Band(kind, prm, h, w["p"])
-    P = cpm.Schwarz(B, c, w["nparts"], w["overlap"], robin=robin, alpha=alpha, alpha_cross=alpha_x)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    u64, i64 = cpm.solve(B, f, P, restart=w["restart"], rtol=w["rtol"], maxit=50000, mixed=False, reorth=0)
-    torch.cuda.synchronize()
-    fp64_s = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    u32, i32 = cpm.solve(B, f, P, **kw)
-    torch.cuda.synchronize()
-    mixed_s = time.perf_counter() - t0
-    diff = ((u32 - u64).norm() / u64.norm()).item()
-    del P, B
-
-    if rank != 0:
-        if world > 1:
-            dist.destroy_process_group()
-        return
-    import json as _j
-    peaks = {}
-    try:
-        peaks = _j.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except OSError:
-        pass
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    alg_bytes = 8.0 * nnz + 4.0 * nloc + 4.0 * n  # FP32 value + int32 column per entry; gather; scatter
-    avg_ms = prec_ms / max(prec_n, 1)
-    achieved = alg_bytes / (avg_ms / 1000.0) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": f"{args.workload}: torus R=1 r=0.4 h={h} p=3 c={c}, {n} band points, "
+        "config": {"workload": f"{args.workload}: torus R=1 r=0.4 h={h} p={w['p']} c={w['c']}, {n} band points, "
                                f"{w['nparts']} parts overlap {w['overlap']} "
-                               f"{'P-ORAS' if robin else 'RAS'} ILU(0), GMRES({w['restart']}) rtol {w['rtol']:g}, "
-                               "classical Gram-Schmidt (one pass), mixed FP32/FP64",
-                   "parallelism": f"replicas x{world}", "l2": "working set (ORAS factors) far above L2"},
-        "solves_per_s": solves_per_s,
-        "iters_per_step": iters / args.steps,
-        "fp64_solve_s": fp64_s, "fp64_iters": i64["iters"], "mixed_solve_s": mixed_s, "mixed_iters": i32["iters"],
-        "mixed_vs_fp64_speedup": fp64_s / mixed_s, "mixed_vs_fp64_rel_diff": diff,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * n, "d2h_bytes_per_step": 2 * 8 * n},
+                               f"{'P-ORAS' if w['robin'] else 'RAS'} ILU(0) (local order {w.get('order', 1)}), "
+                               f"GMRES({w['restart']}) one classical Gram-Schmidt pass, mixed FP32/FP64 to "
+                               f"relative residual {rtol:g}",
+                   "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (Schwarz factors far above 129 MB)"},
+        "solves_per_s": solves_per_s, "iters_per_step": iters / args.steps,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
+                "steps": e_steps},
         "gpu_launches": launches,
-        "roofline": {"kernel": "k_schwarz<float,float> (FP32 Schwarz apply)", "bound": "hbm",
-                     "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": SCHWARZ_TRAFFIC_PER_ENTRY * nnz, "alg_bytes_per_launch": alg_bytes,
-                     "avg_ms": avg_ms},
         "clocks": clk.summary(),
     }
-    if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(w)
-    print(json.dumps(line), flush=True)
+    if not args.quick:
+        line.update(extras(torch, cpm, args, w, f, step, n, rtol))
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        one, allc = cpu_baseline(args.workload)
+        line["cpu_baseline"] = one
+        line["cpu_baseline_all_cores"] = allc
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def extras(torch, cpm, args, w, f, step, n, rtol):
+    """Measurements beside the headline, all outside the timed region."""
+    out = {}
+    peaks = _peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    # one instrumented step: per-apply CUDA-event times of the FP32 Schwarz and operator applies
+    u_mixed, info, (B, P) = step(f, timing=True, keep=True)
+    nnz, nloc = P.total_nnz, P.total_rows
+    sw_ms = info["ms_precond"] / max(info["n_precond"], 1)
+    op_ms = info["ms_operator"] / max(info["n_operator"], 1)
+    alg_sw = 8.0 * nnz + 4.0 * nloc + 4.0 * n     # FP32 value + 16/32-bit column per entry; gather; scatter
+    alg_op = 8.0 * n + 12.0 * B.n_rows            # x in, y out, FP32 offsets of every E row
+    out["roofline"] = {"kernel": "k_schwarz_pk<float,float> (FP32 Schwarz apply)", "bound": "hbm",
+                       "achieved": alg_sw / (sw_ms / 1000.0) / 1e9, "peak": hbm, "unit": "GB/s",
+                       "frac": alg_sw / (sw_ms / 1000.0) / 1e9 / hbm, "traffic": None,
+                       "alg_bytes_per_launch": alg_sw, "avg_ms": sw_ms, "launches_timed": info["n_precond"],
+                       "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+    out["roofline_operator"] = {"kernel": "cpm_apply FP32 (k_erow_grp + k_stencil)", "bound": "hbm",
+                                "achieved": alg_op / (op_ms / 1000.0) / 1e9, "peak": hbm, "unit": "GB/s",
+                                "frac": alg_op / (op_ms / 1000.0) / 1e9 / hbm, "alg_bytes_per_launch": alg_op,
+                                "avg_ms": op_ms}
+    out["schwarz"] = {"stored_entries": nnz, "local_rows": nloc, "max_levels": P.max_levels}
+    # plain FP64 GPU solve of the same system, then continued to the reference tolerance
+    kw64 = dict(restart=w["restart"], maxit=100000, mixed=False, reorth=0)
+    (u64, i64), t64 = _timed(torch, lambda: cpm.solve(B, f, P, rtol=rtol, **kw64))
+    (uref, iref), tref = _timed(torch, lambda: cpm.solve(B, f, P, rtol=REF_RTOL, u0=u64, **kw64))
+    (u32b, i32b), t32b = _timed(torch, lambda: cpm.solve(B, f, P, rtol=rtol, restart=w["restart"], maxit=100000,
+                                                         mixed=True, reorth=0))
+    out["fp64"] = {"solve_s": t64, "iters": i64["iters"], "rel_residual": i64["rel_residual"],
+                   "err_vs_reference": _rel(torch, u64, uref)}
+    out["mixed"] = {"solve_s": t32b, "iters": i32b["iters"], "ir_steps": i32b["ir_steps"],
+                    "rel_residual": i32b["rel_residual"], "err_vs_reference": _rel(torch, u_mixed, uref),
+                    "speedup_vs_fp64": t64 / t32b}
+    out["reference"] = {"rtol": REF_RTOL, "extra_iters": iref["iters"], "extra_s": tref,
+                        "rel_residual": iref["rel_residual"], "what": "GPU FP64 solve continued from the FP64 "
+                        "solution to the reference tolerance (FP64 solves are parity-tested against the oracle)"}
+    del P
+    # BF16 factor storage (ablation)
+    (PB, tb_set) = _timed(torch, lambda: schwarz_for(cpm, B, w, cpm.CPM_BF16))
+    (ub, ib), tb = _timed(torch, lambda: cpm.solve(B, f, PB, rtol=rtol, restart=w["restart"], maxit=100000,
+                                                   mixed=True, reorth=0))
+    out["bf16_factors"] = {"setup_s": tb_set, "solve_s": tb, "iters": ib["iters"], "status": ib["status"],
+                           "rel_residual": ib["rel_residual"], "err_vs_reference": _rel(torch, ub, uref)}
+    del PB, B
+    out["sphere_h0.1"] = sphere_case(torch, cpm)
+    out["pipeline_h0.004"] = pipeline_h004(torch, cpm)
+    return out
+
+
+# ---------------------------------------------------------------- other workloads
+def draw_problems(nprob, hs, seed):
+    """Batched workload: spheres of radius U[0.5, 1.5] and tori R ~ U[0.8,
+    1.2], r ~ U[0.2, 0.5] in turn, spacing drawn from hs, c log-uniform in
+    [0.1, 1000], 1-8 Gaussian right-hand sides; a draw whose band radius
+    would reach 0.9 of the surface's reach moves to the next finer spacing."""
+    u = inputs.uniform(seed, 8 * nprob).reshape(nprob, 8)
+    hs = sorted(hs, reverse=True)
+    out = []
+    for q in range(nprob):
+        sphere = q % 2 == 0
+        if sphere:
+            rho = 0.5 + u[q, 0]
+            params = inputs.surface_params(inputs.SPHERE, a=rho)
+            reach = rho
+        else:
+            R = 0.8 + 0.4 * u[q, 0]
+            r = 0.2 + 0.3 * u[q, 1]
+            params = inputs.surface_params(inputs.TORUS, a=R, b=r)
+            reach = min(r, R - r)
+        k = min(int(u[q, 2] * len(hs)), len(hs) - 1)
+        while k < len(hs) - 1 and math.sqrt(17.0) * hs[k] >= 0.9 * reach:
+            k += 1
+        h = hs[k]
+        if math.sqrt(17.0) * h >= 0.9 * reach:
+            h = reach * 0.9 / math.sqrt(17.0) / 1.01
+        c = 10.0 ** (-1.0 + 4.0 * u[q, 3])
+        nrhs = 1 + min(int(u[q, 4] * 8), 7)
+        out.append(dict(kind=inputs.SPHERE if sphere else inputs.TORUS, params=params, h=h, c=c, nrhs=nrhs,
+                        seed=seed * 1000 + q))
+    return out
+
+
+def run_batch(args):
+    import numpy as np
+    import torch
+
+    from paper_2110_06322_gb300 import cpm
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    hs = [float(x) for x in args.hs.split(",")]
+    specs = draw_problems(args.problems, hs, 4)
+    rows = 13000
+    probs, rhs = [], []
+    t0 = time.perf_counter()
+    for sp in specs:
+        B = cpm.Band(sp["kind"], sp["params"], sp["h"], 3)
+        P = cpm.Schwarz(B, sp["c"], max(1, int(round(B.n_active * 1.15 / rows))), 2, order=2)
+        F = np.stack([inputs.gaussian_vector(sp["seed"] + r, B.n_active) for r in range(sp["nrhs"])])
+        probs.append((B, P, sp["c"]))
+        rhs.append(torch.from_numpy(F).cuda())
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    opts = dict(rtol=1e-8, maxit=100000, mixed=True)
+    cpm.solve_batch(probs[:2], rhs[:2], **opts)
+    L0 = cpm.cpm_kernel_launches()
+    (res, t_batch) = _timed(torch, lambda: cpm.solve_batch(probs, rhs, **opts))
+    launches = cpm.cpm_kernel_launches() - L0
+    U, infos = res
+    pt_iters, q = 0, 0
+    for (b, _, _), f in zip(probs, rhs):
+        for _ in range(f.shape[0]):
+            pt_iters += int(b.n_active) * infos[q]["iters"]
+            q += 1
+
+    def singles():
+        for (B, P, c), f in zip(probs, rhs):
+            for r in range(f.shape[0]):
+                cpm.solve(B, f[r].contiguous(), P, c=c, **opts)
+    (_, t_single) = _timed(torch, singles)
+    n_sys = len(infos)
+    line = {"metric": "batched ORAS-GMRES solves/s (uneven problems, one call)", "value": n_sys / t_batch,
+            "unit": "solves/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"batch: {len(probs)} problems / {n_sys} systems, spacings {hs}, "
+                                   f"{min(int(b.n_active) for b, _, _ in probs)}-"
+                                   f"{max(int(b.n_active) for b, _, _ in probs)} band points, c log-uniform "
+                                   "0.1-1000, 1-8 right-hand sides, mixed FP32/FP64 to 1e-8"},
+            "setup_s": t_setup, "batch_s": t_batch, "single_s": t_single, "batch_speedup": t_single / t_batch,
+            "band_pt_iters_per_s": pt_iters / t_batch, "iters_max": max(i["iters"] for i in infos),
+            "iters_total": sum(i["iters"] for i in infos),
+            "converged": sum(1 for i in infos if i["status"] == 0),
+            "worst_rel_residual": max(i["rel_residual"] for i in infos), "gpu_launches": launches}
+    print(json.dumps(line), flush=True)
+
+
+def schnakenberg_initial_state(w, n):
+    """Initial state of the differentiable workload: the homogeneous steady
+    state (u*, v*) = (delta1 + delta2, delta2 / (u*^2 + lambda)) of eq. schnack
+    with delta1 = 0.003, delta2 = 0.7, lambda = 0.06, times 1 + 0.01 U[-1, 1]
+    per node (seeds w["seed"] for u and w["seed"] + 1 for v)."""
+    us = 0.003 + 0.7
+    vs = 0.7 / (us * us + 0.06)
+    a = inputs.uniform(w["seed"], n)
+    b = inputs.uniform(w["seed"] + 1, n)
+    return us * (1.0 + 0.01 * (2.0 * a - 1.0)), vs * (1.0 + 0.01 * (2.0 * b - 1.0)), us, vs
+
+
+def run_schnakenberg(args):
+    import torch
+
+    from paper_2110_06322_gb300 import autograd, cpm
+    w = workload("schnakenberg_torus_h0.005")
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    t0 = time.perf_counter()
+    B = cpm.Band(w["kind"], w["params"], w["h"], w["p"])
+    opts = dict(rtol=args.rtol or w["rtol"], restart=w["restart"], maxit=50000, mixed=True)
+    sim = autograd.Schnakenberg(B, dt=w["dt"], nparts=w["nparts"], overlap=w["overlap"], robin=w["robin"], **opts)
+    n = B.n_active
+    u0, v0, us, vs = schnakenberg_initial_state(w, n)
+    u0, v0 = torch.from_numpy(u0).to(dev), torch.from_numpy(v0).to(dev)
+    cu, cv = sim.shifts(w["Du"], w["Dv"])
+    sim._pc(cu)
+    sim._pc(cv)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    steps = min(args.steps, w["steps"]) if args.steps else w["steps"]
+    ut, vt = u0.clone().requires_grad_(True), v0.clone().requires_grad_(True)
+    Du = torch.tensor(w["Du"], dtype=torch.float64, device=dev, requires_grad=True)
+    Dv = torch.tensor(w["Dv"], dtype=torch.float64, device=dev, requires_grad=True)
+    s0 = sim.solves
+    ((uN, vN), t_fwd) = _timed(torch, lambda: sim.run(ut, vt, Du, Dv, steps=steps, checkpoint=w["checkpoint"]))
+    loss = 0.5 * (((uN - us) ** 2).sum() + ((vN - vs) ** 2).sum())
+    s1 = sim.solves
+    (_, t_bwd) = _timed(torch, lambda: loss.backward())
+    line = {"metric": "differentiable Schnakenberg steps/s (forward and checkpointed adjoint)",
+            "value": steps / (t_fwd + t_bwd), "unit": "steps/s", "n_gpus": 1, "higher_is_better": True,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"schnakenberg torus h={w['h']} ({n} band points), D=({w['Du']}, {w['Dv']}), "
+                                   f"dt={w['dt']}, {steps} steps, checkpoints every {w['checkpoint']}"},
+            "setup_s": t_setup, "forward_s": t_fwd, "backward_s": t_bwd, "forward_solves": s1 - s0,
+            "backward_solves": sim.solves - s1, "loss": loss.item(), "dL_dDu": Du.grad.item(),
+            "dL_dDv": Dv.grad.item(), "grad_u0_norm": ut.grad.norm().item(), "rtol": opts["rtol"]}
+    if args.fd_steps > 0:
+        k = args.fd_steps
+        ut2, vt2 = u0.clone().requires_grad_(True), v0.clone().requires_grad_(True)
+        Du2 = torch.tensor(w["Du"], dtype=torch.float64, device=dev, requires_grad=True)
+        Dv2 = torch.tensor(w["Dv"], dtype=torch.float64, device=dev, requires_grad=True)
+        uK, vK = sim.run(ut2, vt2, Du2, Dv2, steps=k, checkpoint=w["checkpoint"])
+        (0.5 * (((uK - us) ** 2).sum() + ((vK - vs) ** 2).sum())).backward()
+
+        def loss_of(du, dv):
+            with torch.no_grad():
+                uu, vv = sim.run(u0, v0, du, dv, steps=k)
+            return 0.5 * float(((uu - us) ** 2).sum() + ((vv - vs) ** 2).sum())
+        fd = {}
+        for name, grad in (("Du", Du2.grad.item()), ("Dv", Dv2.grad.item())):
+            eps = 1e-4 * w[name]
+            hi, lo = {"Du": w["Du"], "Dv": w["Dv"]}, {"Du": w["Du"], "Dv": w["Dv"]}
+            hi[name] += eps
+            lo[name] -= eps
+            cd = (loss_of(hi["Du"], hi["Dv"]) - loss_of(lo["Du"], lo["Dv"])) / (2 * eps)
+            fd[name] = {"adjoint": grad, "central_difference": cd, "rel_diff": abs(grad - cd) / abs(cd)}
+        line["fd_check"] = {"steps": k, **fd}
+    print(json.dumps(line), flush=True)
+
+
+def run_profile(args):
+    """Bare loops for ncu captures: no clock sampler, no oracle, nothing else on
+    the GPU.  Prints the library's kernel launches per step."""
+    import torch
+
+    from paper_2110_06322_gb300 import cpm
+    w = workload(args.workload)
+    torch.cuda.set_device(0)
+    L0 = cpm.cpm_kernel_launches()
+    B0 = cpm.Band(w["kind"], w["params"], w["h"], w["p"])
+    cp = B0.export()[3][: B0.n_active].cpu().numpy()
+    f_h, g_h = rhs_pair(cp, w)
+    f, g = torch.from_numpy(f_h).cuda(), torch.from_numpy(g_h).cuda()
+    del B0
+    torch.cuda.synchronize()
+    print(f"inputs launches={cpm.cpm_kernel_launches() - L0}", flush=True)
+    if args.profile in ("op", "opT", "pc"):
+        B = cpm.Band(w["kind"], w["params"], w["h"], w["p"])
+        x = f.float()
+        y = torch.empty_like(x)
+        if args.profile == "pc":
+            P = schwarz_for(cpm, B, w, cpm.CPM_F32)
+            run = lambda: P.apply(x, out=y)  # noqa: E731
+        else:
+            tr = args.profile == "opT"
+            run = lambda: B.apply(w["c"], x, transpose=tr, out=y)  # noqa: E731
+        run()  # first use builds the transpose map
+        torch.cuda.synchronize()
+        for q in range(args.warmup + args.steps):
+            L1 = cpm.cpm_kernel_launches()
+            run()
+            torch.cuda.synchronize()
+            print(f"apply step {q}: launches={cpm.cpm_kernel_launches() - L1}", flush=True)
+        return
+    kw = dict(restart=w["restart"], rtol=w["solve_rtol"], maxit=args.maxit, mixed=True, inner_rtol=1e-4, reorth=0)
+    for q in range(args.warmup + args.steps):
+        L1 = cpm.cpm_kernel_launches()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        ev[0].record()
+        B = cpm.Band(w["kind"], w["params"], w["h"], w["p"])
+        ev[1].record()
+        P = schwarz_for(cpm, B, w, cpm.CPM_F32)
+        ev[2].record()
+        if args.profile == "setup":
+            B.apply(w["c"], f.float(), transpose=True)
+            ev[3].record()
+            P.apply(f.float(), transpose=True)
+            ev[4].record()
+        else:
+            u, i1 = cpm.solve(B, f, P, **kw)
+            ev[3].record()
+            lam, i2 = cpm.solve(B, g, P, adjoint=True, **kw)
+            ev[4].record()
+        torch.cuda.synchronize()
+        ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(4)]
+        extra = "" if args.profile == "setup" else f" iters={i1['iters']}+{i2['iters']}"
+        print(f"step {q}: N_A={B.n_active} band {ms[0]:.1f} ms, schwarz {ms[1]:.1f} ms, then {ms[2]:.1f} + "
+              f"{ms[3]:.1f} ms{extra}, launches={cpm.cpm_kernel_launches() - L1}", flush=True)
+        del P, B
 
 
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.profile:
+        run_profile(args)
+    elif args.workload == "batch":
+        run_batch(args)
+    elif args.workload == "schnakenberg":
+        run_schnakenberg(args)
     else:
         run_gpu(args)
 

@@ -79,6 +79,8 @@ typedef struct oras_pc oras_pc;
  * Returns CPM_ERR_BAND when lambda >= the reach kappa^-1 (sphere rho, torus
  * min(r, R - r)) or when some E-row cube leaves Sigma_A. */
 cpm_status cpm_band_build(const cpm_surface* surf, double h, int p, void* stream, cpm_band** out);
+/* (cpm_band_build also commits, once per device, the fixed scratch array of
+ * cpm_apply_noalloc below.) */
 
 /* Sizes of the band: |Sigma_A|, |Sigma_G|, |T|. Host pointers; any may be NULL. */
 cpm_status cpm_band_info(const cpm_band* band, int64_t* n_active, int64_t* n_ghost, int64_t* n_tube);
@@ -120,14 +122,18 @@ cpm_status cpm_apply(const cpm_band* band, const double* c, const void* x, void*
  * framework's caching pool that has reserved the device) or latency-bounded
  * loops in which an allocation may block.  This is not an operation of the
  * paper; it only changes where the apply's scratch comes from.
- *   Scratch: one fixed 16 MiB array inside the library, held by every device
- *   that loads it until the process exits.  A call needs
+ *   Scratch: one fixed 16 MiB array inside the library.  It is committed on a
+ *   device when the first band is built there (cpm_band_build looks up the
+ *   array's device address with that device current, which under CUDA's lazy
+ *   module loading is what loads it) and held until the process exits, so a
+ *   caller that builds its bands before handing the device to another
+ *   allocator needs no allocation later.  A call needs
  *   min(nrhs, 16) x N_C x 8 bytes (N_C = N_A + N_G); larger calls are rejected
- *   with CPM_ERR_ARG and a message naming the sizes.
- *   The first call on a device looks up the array's device address (with
- *   that device current); make that first call before any stream capture.
+ *   with CPM_ERR_ARG and a message naming the sizes.  More than 16 right-hand
+ *   sides run 16 at a time through the same scratch.
  *   All calls share the array: calls whose kernels overlap on the GPU race.
- *   Allocates nothing (no cudaMalloc, no stream-ordered or library allocation). */
+ *   Allocates nothing (no cudaMalloc, no stream-ordered or library allocation;
+ *   cpm_device_allocations() does not change). */
 cpm_status cpm_apply_noalloc(const cpm_band* band, const double* c, const void* x, void* y, cpm_dtype dtype,
                              int nrhs, void* stream);
 
@@ -151,13 +157,17 @@ typedef struct {
   int32_t store;
   int32_t order;  /* local order of the ILU(0) factorisation: 1 descending distance
                      to the surface; 2 distance shells of width h (outermost
-                     first), then lattice-parity colours; ties canonical */
+                     first), then lattice-parity colours; ties canonical;
+                     0 by degree: 2 for p = 3 (fewer GMRES iterations and
+                     shallower sweeps), 1 for p = 2 (where the shell order
+                     costs iterations) */
 } oras_params;
 
 /* oras_setup -- partition, overlap growth, local matrices A_j = R_j M R_j^T
  * (+ Robin term), and ILU(0) of each A_j in its local order (prm->order: 1
  * descending distance to the surface, ties by canonical index; 2 distance
- * shells of width h, then lattice-parity colours).  c is the shift of M.
+ * shells of width h, then lattice-parity colours; 0 chosen by the degree p).
+ * c is the shift of M.
  * The paper leaves the local order to PETSc (Section 4.1.1). */
 cpm_status oras_setup(const cpm_band* band, const oras_params* prm, double c, void* stream, oras_pc** out);
 
@@ -168,6 +178,29 @@ cpm_status oras_setup(const cpm_band* band, const oras_params* prm, double c, vo
  * dtype (CPM_F64 or CPM_F32), not overlapping. */
 cpm_status oras_apply(const oras_pc* pc, const void* r, void* z, cpm_dtype dtype, int nrhs, int transpose,
                       void* stream);
+
+/* Run-time settings of a preconditioner's apply.  None changes the result of
+ * a successful apply; they choose among equivalent kernels and exercise the
+ * failure path.  The paper has no counterpart (its subdomain solves are PETSc
+ * calls, Section 4.1.1).
+ *   xplace         where each subdomain's local vector lives during the
+ *                  triangular sweeps: 0 in shared memory when it fits beside the
+ *                  factor ring (default), 1 always in a global-memory slice
+ *   probe_timeout  0 normal; 1 failure-path test: the first factor-chunk wait
+ *                  of every subdomain waits on a barrier that nothing completes,
+ *                  so each CTA runs out after wait_polls polls, waits for its
+ *                  copies in flight and returns; the next cpm_solve reports
+ *                  CPM_ERR_TIMEOUT (the GPU context stays usable)
+ *   wait_polls     polls of each consumer-side bounded wait before it gives up
+ *                  (0: the default, 2^22 polls, seconds at most)
+ * pc: library-owned handle; t: HOST pointer.  Not stream-ordered: set it
+ * while no apply of pc is running. */
+typedef struct {
+  int32_t xplace;
+  int32_t probe_timeout;
+  int64_t wait_polls;
+} oras_tuning;
+cpm_status oras_set_tuning(oras_pc* pc, const oras_tuning* t);
 
 /* Sizes of the preconditioner: number of parts, sum of |S_j|, sum of nnz(A_j),
  * and the largest number of forward-solve levels of any subdomain.  Host pointers. */
@@ -296,6 +329,11 @@ void oras_free(oras_pc* pc);
  * (all threads).  The difference of two readings counts the kernels of the
  * calls made in between. */
 int64_t cpm_kernel_launches(void);
+
+/* Total number of device allocations (stream-ordered cudaMallocAsync calls)
+ * this library has made since it was loaded (all threads).  The difference of
+ * two readings counts the allocations of the calls made in between. */
+int64_t cpm_device_allocations(void);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* cpm_last_error(void);

@@ -5,6 +5,5 @@ Modules (imported explicitly; nothing here loads the CUDA library):
   autograd     differentiable solves and the checkpointed Schnakenberg integrator
   inputs       seeded synthetic inputs and the named workloads
   build        in-tree nvcc build of libcpm.so
-  profile_step, batch_bench, rd_gradient, scale_case
-               drivers for profiling and measurement runs
+(The measurement and profiling drivers are modes of bench.py at the repository root.)
 """

@@ -36,6 +36,10 @@ class oras_params(C.Structure):
                 ("alpha_cross", C.c_double), ("store", C.c_int32), ("order", C.c_int32)]
 
 
+class oras_tuning(C.Structure):
+    _fields_ = [("xplace", C.c_int32), ("probe_timeout", C.c_int32), ("wait_polls", C.c_int64)]
+
+
 class cpm_solve_params(C.Structure):
     _fields_ = [("restart", C.c_int32), ("maxit", C.c_int32), ("rtol", C.c_double), ("mixed", C.c_int32),
                 ("reorth", C.c_int32), ("inner_rtol", C.c_double), ("timing", C.c_int32)]
@@ -78,6 +82,8 @@ def lib():
         "oras_setup": (i32, [vp, P(oras_params), f64, vp, P(vp)]),
         "oras_apply": (i32, [vp, vp, vp, i32, i32, i32, vp]),
         "oras_info": (i32, [vp, P(C.c_int32), P(C.c_int64), P(C.c_int64), P(C.c_int32)]),
+        "oras_set_tuning": (i32, [vp, P(oras_tuning)]),
+        "cpm_device_allocations": (C.c_int64, []),
         "oras_export": (i32, [vp, vp, vp, vp, vp]),
         "cpm_solve": (i32, [vp, vp, f64, vp, vp, P(cpm_solve_params), P(cpm_solve_info), vp]),
         "cpm_solve_adjoint": (i32, [vp, vp, f64, vp, vp, P(cpm_solve_params), P(cpm_solve_info), vp]),
@@ -100,9 +106,9 @@ def lib():
 
 
 EXPORTED = ["cpm_last_error", "cpm_band_build", "cpm_band_info", "cpm_band_export", "cpm_band_weights", "cpm_apply",
-            "oras_setup", "oras_apply", "oras_info", "oras_export", "cpm_solve", "cpm_solve_adjoint", "cpm_band_free",
-            "oras_free", "cpm_kernel_launches", "cpm_apply_noalloc", "cpm_imex_rhs", "cpm_imex_rhs_adjoint",
-            "cpm_dot", "cpm_solve_batch"]
+            "oras_setup", "oras_apply", "oras_info", "oras_set_tuning", "oras_export", "cpm_solve",
+            "cpm_solve_adjoint", "cpm_band_free", "oras_free", "cpm_kernel_launches", "cpm_device_allocations",
+            "cpm_apply_noalloc", "cpm_imex_rhs", "cpm_imex_rhs_adjoint", "cpm_dot", "cpm_solve_batch"]
 
 
 def _check(st):
@@ -139,19 +145,44 @@ def cpm_band_build(kind, params, h, p=3, stream=None):
     return out
 
 
+def _apply_args(band, c, x, y):
+    """nrhs and the host array of shifts of an operator apply, after checking
+    that x and y are matching device vectors of whole right-hand sides."""
+    n = Band.n_active_of(band)
+    code = _dtype_code(x)
+    if x.numel() == 0 or x.numel() % n != 0:
+        raise ValueError(f"x holds {x.numel()} values, not a whole number of {n}-node vectors")
+    nrhs = x.numel() // n
+    if y.numel() != x.numel() or y.dtype != x.dtype or y.device != x.device:
+        raise ValueError("y must match x in size, dtype and device")
+    if not (x.is_contiguous() and y.is_contiguous()):
+        raise ValueError("x and y must be contiguous")
+    cl = [float(c)] * nrhs if not hasattr(c, "__len__") else [float(v) for v in c]
+    if len(cl) != nrhs:
+        raise ValueError(f"{len(cl)} shifts given for {nrhs} right-hand sides")
+    return nrhs, code, (C.c_double * nrhs)(*cl)
+
+
 def cpm_apply(band, c, x, y, transpose=False, stream=None):
-    nrhs = x.numel() // Band.n_active_of(band)
-    cs = (C.c_double * nrhs)(*([float(c)] * nrhs if not hasattr(c, "__len__") else [float(v) for v in c]))
-    _check(lib().cpm_apply(band, cs, _ptr(x), _ptr(y), _dtype_code(x), nrhs, int(bool(transpose)), _stream(stream)))
+    nrhs, code, cs = _apply_args(band, c, x, y)
+    _check(lib().cpm_apply(band, cs, _ptr(x), _ptr(y), code, nrhs, int(bool(transpose)), _stream(stream)))
     return y
 
 
 def cpm_apply_noalloc(band, c, x, y, stream=None):
     """y = M x through the entry point that allocates nothing (fixed library scratch)."""
-    nrhs = x.numel() // Band.n_active_of(band)
-    cs = (C.c_double * nrhs)(*([float(c)] * nrhs if not hasattr(c, "__len__") else [float(v) for v in c]))
-    _check(lib().cpm_apply_noalloc(band, cs, _ptr(x), _ptr(y), _dtype_code(x), nrhs, _stream(stream)))
+    nrhs, code, cs = _apply_args(band, c, x, y)
+    _check(lib().cpm_apply_noalloc(band, cs, _ptr(x), _ptr(y), code, nrhs, _stream(stream)))
     return y
+
+
+def cpm_device_allocations():
+    return lib().cpm_device_allocations()
+
+
+def oras_set_tuning(pc, xplace=0, probe_timeout=0, wait_polls=0):
+    t = oras_tuning(int(xplace), int(probe_timeout), int(wait_polls))
+    _check(lib().oras_set_tuning(pc, C.byref(t)))
 
 
 def _rx(prm):
@@ -177,7 +208,7 @@ def cpm_dot(band, a, b, out, stream=None):
     return out
 
 
-def oras_setup(band, c, nparts, overlap, robin=False, alpha=4.0, alpha_cross=20.0, store=CPM_F32, order=1,
+def oras_setup(band, c, nparts, overlap, robin=False, alpha=4.0, alpha_cross=20.0, store=CPM_F32, order=0,
                stream=None):
     prm = oras_params(int(nparts), int(overlap), int(bool(robin)), float(alpha), float(alpha_cross), int(store),
                       int(order))
@@ -294,7 +325,7 @@ class Band:
 class Schwarz:
     """(O)RAS preconditioner over a Band (Section 2.2)."""
 
-    def __init__(self, band, c, nparts, overlap, robin=False, alpha=4.0, alpha_cross=20.0, store=CPM_F32, order=1,
+    def __init__(self, band, c, nparts, overlap, robin=False, alpha=4.0, alpha_cross=20.0, store=CPM_F32, order=0,
                  stream=None):
         self.band = band
         self.c = float(c)
@@ -312,6 +343,11 @@ class Schwarz:
     def apply(self, r, transpose=False, out=None, stream=None):
         z = torch.empty_like(r) if out is None else out
         return oras_apply(self.handle, r, z, self.band.n_active, transpose, stream)
+
+    def set_tuning(self, xplace=0, probe_timeout=0, wait_polls=0):
+        """Run-time settings of the apply (oras_set_tuning): local-vector
+        placement, the failure-path probe and the wait bound."""
+        oras_set_tuning(self.handle, xplace, probe_timeout, wait_polls)
 
     def export(self, stream=None):
         d = self.band.device

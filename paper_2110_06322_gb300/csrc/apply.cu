@@ -124,6 +124,142 @@ __global__ void __launch_bounds__(256) k_erow_apply(ApplyGeom G, const T* __rest
   }
 }
 
+// Pass 1 in FP32, grouped by cube: the rows that share an interpolation
+// cube (about five per cube on the benchmark surfaces: the nodes along one
+// surface normal) are consecutive in the cube-base order, and one thread
+// takes a work item of up to EGROUP_MAX of them.  It gathers the (p+1)^3 cube
+// values once into registers (minus the reference node's value, the
+// difference form above), then evaluates each of its rows from registers with
+// that row's weights.  The arithmetic per row is the one of k_erow_apply, in
+// the same order; only the loads are shared.
+constexpr int EGROUP_MAX = 16;
+constexpr int EGROUP_WIN = 256;  // items are ordered by row count within windows of this many
+
+template <int P>
+__global__ void __launch_bounds__(EGROUP_WIN)
+    k_erow_grp(ApplyGeom G, int64_t nitem, const int2* __restrict__ items, const int32_t* __restrict__ grow,
+               const float* __restrict__ gs, const float* __restrict__ x, float* __restrict__ w) {
+  const int rhs = blockIdx.y;
+  x += (int64_t)rhs * G.nA;
+  w += (int64_t)rhs * G.nR * 2;
+  for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < nitem;
+       it += (int64_t)gridDim.x * blockDim.x) {
+    const int2 I = items[it];
+    const int start = I.x >> 4, rows = (I.x & 15) + 1;
+    const int b0 = G.ijkA[3 * I.y], b1 = G.ijkA[3 * I.y + 1], b2 = G.ijkA[3 * I.y + 2];
+    float X[P + 1][P + 1][P + 1];
+#pragma unroll
+    for (int u = 0; u <= P; ++u)
+#pragma unroll
+      for (int v = 0; v <= P; ++v) {
+        const float* xp = x + bm_rank_known(G.amap, G.g, b0 + u, b1 + v, b2);
+#pragma unroll
+        for (int t = 0; t <= P; ++t) X[u][v][t] = __ldg(xp + t);
+      }
+    const float xref = X[1][1][1];
+#pragma unroll
+    for (int u = 0; u <= P; ++u)
+#pragma unroll
+      for (int v = 0; v <= P; ++v)
+#pragma unroll
+        for (int t = 0; t <= P; ++t) X[u][v][t] -= xref;
+    for (int k = 0; k < rows; ++k) {
+      const int pos = start + k;
+      const int32_t r = grow[pos];
+      float l[3][P + 1];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) lagrange_f32<P>(gs[3 * pos + d], l[d]);
+      float acc = 0;
+#pragma unroll
+      for (int u = 0; u <= P; ++u) {
+        float au = 0;
+#pragma unroll
+        for (int v = 0; v <= P; ++v) {
+          float av = 0;
+#pragma unroll
+          for (int t = 0; t <= P; ++t) av += l[2][t] * X[u][v][t];
+          au += l[1][v] * av;
+        }
+        acc += l[0][u] * au;
+      }
+      w[2 * r] = acc;
+      w[2 * r + 1] = xref;
+    }
+  }
+}
+
+// ---- grouping of the E rows by cube (set-up, at band build)
+// key of row r: canonical rank of its cube base (a node of Sigma_A: the
+// cube lies inside Sigma_A); count rows per key
+__global__ void k_gkey(ApplyGeom G, int32_t* key, int32_t* cnt) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < G.nR; r += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t q = bm_rank_known(G.amap, G.g, G.rbase[3 * r], G.rbase[3 * r + 1], G.rbase[3 * r + 2]);
+    key[r] = q;
+    atomicAdd(&cnt[q], 1);
+  }
+}
+__global__ void k_gfill(int64_t nR, const int32_t* __restrict__ key, const int64_t* __restrict__ kptr,
+                        int32_t* cursor, int32_t* grow) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nR; r += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t q = key[r];
+    grow[kptr[q] + atomicAdd(&cursor[q], 1)] = (int32_t)r;
+  }
+}
+// per cube: its rows ascending (the fill order above is not deterministic),
+// and its number of work items
+__global__ void k_gsort(int64_t nA, const int64_t* __restrict__ kptr, int32_t* grow, int32_t* icnt) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nA; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = kptr[q], n = kptr[q + 1] - a;
+    for (int64_t i = a + 1; i < a + n; ++i) {
+      const int32_t v = grow[i];
+      int64_t j = i - 1;
+      while (j >= a && grow[j] > v) {
+        grow[j + 1] = grow[j];
+        --j;
+      }
+      grow[j + 1] = v;
+    }
+    icnt[q] = (int32_t)((n + EGROUP_MAX - 1) / EGROUP_MAX);
+  }
+}
+__global__ void k_gitems(int64_t nA, const int64_t* __restrict__ kptr, const int64_t* __restrict__ iptr, int2* items) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nA; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = kptr[q], n = kptr[q + 1] - a;
+    int64_t o = iptr[q];
+    for (int64_t c = 0; c < n; c += EGROUP_MAX, ++o) {
+      const int64_t rows = n - c < EGROUP_MAX ? n - c : EGROUP_MAX;
+      items[o] = make_int2((int)(((a + c) << 4) | (rows - 1)), (int)q);
+    }
+  }
+}
+// within each window of EGROUP_WIN consecutive items, order the items by
+// row count (stable), so that the threads of a warp loop over similar counts
+// while the window keeps its spatial locality
+__global__ void __launch_bounds__(EGROUP_WIN) k_gwin(int64_t nitem, const int2* __restrict__ in, int2* out) {
+  __shared__ int2 sh[EGROUP_WIN];
+  const int64_t w0 = (int64_t)blockIdx.x * EGROUP_WIN;
+  const int n = (int)(nitem - w0 < EGROUP_WIN ? nitem - w0 : EGROUP_WIN);
+  const int t = threadIdx.x;
+  if (t < n) sh[t] = in[w0 + t];
+  __syncthreads();
+  if (t < n) {
+    const int mine = sh[t].x & 15;
+    int pos = 0;
+    for (int k = 0; k < n; ++k) {
+      const int o = sh[k].x & 15;
+      pos += (o < mine || (o == mine && k < t)) ? 1 : 0;
+    }
+    out[w0 + pos] = sh[t];
+  }
+}
+__global__ void k_gs32(int64_t nR, const int32_t* __restrict__ grow, const float* __restrict__ s32, float* gs) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nR; p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = grow[p];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) gs[3 * p + d] = s32[3 * r + d];
+  }
+}
+
 // Pass 2: y_i = (c + 6/h^2) x_i - (1/h^2) sum_n w_n.
 template <typename T>
 __global__ void __launch_bounds__(256) k_stencil(ApplyGeom G, Shifts S, const T* __restrict__ x,
@@ -314,6 +450,23 @@ ApplyGeom geom_of(const cpm_band* B) {
   return G;
 }
 
+// Pass 1 for nr right-hand sides: FP64 row by row (weights precomputed,
+// FP64-ALU bound); FP32 grouped by cube.
+template <typename T>
+cpm_status erow_pass(const cpm_band* B, const ApplyGeom& G, const T* x, T* w, int nr, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    dim3 g1(grid_for(B->nitem, EGROUP_WIN), nr);
+    const int2* it = reinterpret_cast<const int2*>(B->gitem);
+    if (B->p == 3) KL(k_erow_grp<3><<<g1, EGROUP_WIN, 0, s>>>(G, B->nitem, it, B->grow, B->gs32, x, w));
+    else KL(k_erow_grp<2><<<g1, EGROUP_WIN, 0, s>>>(G, B->nitem, it, B->grow, B->gs32, x, w));
+  } else {
+    dim3 g1(grid_for(B->nR, 256), nr);
+    if (B->p == 3) KL(k_erow_apply<T, 3><<<g1, 256, 0, s>>>(G, x, w));
+    else KL(k_erow_apply<T, 2><<<g1, 256, 0, s>>>(G, x, w));
+  }
+  return CPM_OK;
+}
+
 template <typename T>
 cpm_status apply_typed(const cpm_band* B, const double* c, const T* x, T* y, int nrhs, int transpose, cudaStream_t s) {
   ApplyGeom G = geom_of(B);
@@ -327,9 +480,8 @@ cpm_status apply_typed(const cpm_band* B, const double* c, const T* x, T* y, int
     const T* xr = x + (int64_t)r0 * B->nA;
     T* yr = y + (int64_t)r0 * B->nA;
     if (!transpose) {
-      dim3 g1(grid_for(B->nR, 256), nr), g2(grid_for(B->nA, 256), nr);
-      if (B->p == 3) KL(k_erow_apply<T, 3><<<g1, 256, 0, s>>>(G, xr, w));
-      else KL(k_erow_apply<T, 2><<<g1, 256, 0, s>>>(G, xr, w));
+      CPM_TRY(erow_pass(B, G, xr, w, nr, s));
+      dim3 g2(grid_for(B->nA, 256), nr);
       KL(k_stencil<T><<<g2, 256, 0, s>>>(G, S, xr, w, yr));
     } else {
       dim3 g1(grid_for(B->nR, 256), nr);
@@ -355,9 +507,8 @@ cpm_status apply_fwd_scratch(const cpm_band* B, const double* c, const T* x, T* 
     for (int q = 0; q < nr; ++q) S.c[q] = c[r0 + q];
     const T* xr = x + (int64_t)r0 * B->nA;
     T* yr = y + (int64_t)r0 * B->nA;
-    dim3 g1(grid_for(B->nR, 256), nr), g2(grid_for(B->nA, 256), nr);
-    if (B->p == 3) KL(k_erow_apply<T, 3><<<g1, 256, 0, s>>>(G, xr, w));
-    else KL(k_erow_apply<T, 2><<<g1, 256, 0, s>>>(G, xr, w));
+    CPM_TRY(erow_pass(B, G, xr, w, nr, s));
+    dim3 g2(grid_for(B->nA, 256), nr);
     KL(k_stencil<T><<<g2, 256, 0, s>>>(G, S, xr, w, yr));
     CPM_CUDA(cudaGetLastError());
   }
@@ -374,6 +525,48 @@ cpm_status apply_op_scratch(const cpm_band* B, const double* c, const void* x, v
     return apply_fwd_scratch<double>(B, c, (const double*)x, (double*)y, nrhs, (double*)scratch, s);
   if (dt == CPM_F32) return apply_fwd_scratch<float>(B, c, (const float*)x, (float*)y, nrhs, (float*)scratch, s);
   return fail(CPM_ERR_ARG, "cpm_apply_noalloc supports CPM_F64 and CPM_F32 vectors");
+}
+
+cpm_status build_erow_groups(cpm_band* B, cudaStream_t s) {
+  ApplyGeom G = geom_of(B);
+  const int64_t nA = B->nA, nR = B->nR;
+  int32_t *key = nullptr, *cnt = nullptr, *icnt = nullptr;
+  int64_t *kptr = nullptr, *iptr = nullptr;
+  int2* tmp = nullptr;
+  auto done = [&](cpm_status st) {
+    dfree(key, s);
+    dfree(cnt, s);
+    dfree(icnt, s);
+    dfree(kptr, s);
+    dfree(iptr, s);
+    dfree(tmp, s);
+    return st;
+  };
+  cpm_status st;
+  if ((st = dalloc(&key, nR, s)) != CPM_OK) return done(st);
+  if ((st = dalloc(&cnt, nA, s)) != CPM_OK) return done(st);
+  if ((st = dalloc(&icnt, nA, s)) != CPM_OK) return done(st);
+  if ((st = dalloc(&kptr, nA + 1, s)) != CPM_OK) return done(st);
+  if ((st = dalloc(&iptr, nA + 1, s)) != CPM_OK) return done(st);
+  if ((st = dalloc(&B->grow, nR, s)) != CPM_OK) return done(st);
+  if ((st = dalloc(&B->gs32, 3 * nR, s)) != CPM_OK) return done(st);
+  CPM_CUDA(cudaMemsetAsync(cnt, 0, nA * sizeof(int32_t), s));
+  KL(k_gkey<<<grid_for(nR, 256), 256, 0, s>>>(G, key, cnt));
+  if ((st = scan_exclusive_i32(cnt, kptr, nA, s)) != CPM_OK) return done(st);
+  CPM_CUDA(cudaMemsetAsync(cnt, 0, nA * sizeof(int32_t), s));
+  KL(k_gfill<<<grid_for(nR, 256), 256, 0, s>>>(nR, key, kptr, cnt, B->grow));
+  KL(k_gsort<<<grid_for(nA, 256), 256, 0, s>>>(nA, kptr, B->grow, icnt));
+  if ((st = scan_exclusive_i32(icnt, iptr, nA, s)) != CPM_OK) return done(st);
+  CPM_CUDA(cudaMemcpyAsync(&B->nitem, iptr + nA, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  CPM_CUDA(cudaStreamSynchronize(s));
+  if ((st = dalloc(&tmp, B->nitem, s)) != CPM_OK) return done(st);
+  if ((st = dalloc(&B->gitem, 2 * B->nitem, s)) != CPM_OK) return done(st);
+  KL(k_gitems<<<grid_for(nA, 256), 256, 0, s>>>(nA, kptr, iptr, tmp));
+  const int64_t nwin = (B->nitem + EGROUP_WIN - 1) / EGROUP_WIN;
+  KL(k_gwin<<<(unsigned)nwin, EGROUP_WIN, 0, s>>>(B->nitem, tmp, reinterpret_cast<int2*>(B->gitem)));
+  KL(k_gs32<<<grid_for(nR, 256), 256, 0, s>>>(nR, B->grow, B->s32, B->gs32));
+  CPM_CUDA(cudaGetLastError());
+  return done(CPM_OK);
 }
 
 cpm_status build_transpose_map(cpm_band* B, cudaStream_t s) {

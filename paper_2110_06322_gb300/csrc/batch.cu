@@ -603,9 +603,8 @@ cpm_status solve_batch(int nprob, const cpm_band* const* bands, const oras_pc* c
   if (e != cudaSuccess) return bail(cuda_fail(e, "batched solve", __FILE__, __LINE__));
   for (int p = 0; p < nprob; ++p)
     if (Bt.pc[p]) {
-      int herr = 0;
-      cudaMemcpy(&herr, Bt.pc[p]->err, sizeof(int), cudaMemcpyDeviceToHost);
-      if (herr) return bail(fail(CPM_ERR_TIMEOUT, "a bounded wait in the Schwarz apply ran out"));
+      const cpm_status te = oras_take_error(Bt.pc[p], s);
+      if (te != CPM_OK) return bail(te);
     }
   cpm_status all = CPM_OK;
   for (int q = 0; q < S; ++q) {

@@ -11,6 +11,7 @@ namespace cpm {
 
 static thread_local char g_err[512] = "";
 std::atomic<long long> g_launches{0};
+std::atomic<long long> g_allocs{0};
 
 void set_error(const char* fmt, ...) {
   va_list ap;
@@ -61,9 +62,21 @@ const char* cpm_last_error(void) { return g_err; }
 
 int64_t cpm_kernel_launches(void) { return (int64_t)g_launches.load(); }
 
+int64_t cpm_device_allocations(void) { return (int64_t)g_allocs.load(); }
+
 cpm_status cpm_band_build(const cpm_surface* surf, double h, int p, void* stream, cpm_band** out) {
   g_err[0] = 0;
-  return band_build(surf, h, p, as_stream(stream), out);
+  cpm_status st = band_build(surf, h, p, as_stream(stream), out);
+  if (st != CPM_OK) return st;
+  // commit cpm_apply_noalloc's fixed scratch on this device now, while the
+  // caller is still allocating (lazy module loading would otherwise commit
+  // it at the first cpm_apply_noalloc call)
+  st = noalloc_prepare();
+  if (st != CPM_OK) {
+    band_free(*out, as_stream(stream));
+    *out = nullptr;
+  }
+  return st;
 }
 
 cpm_status cpm_band_info(const cpm_band* band, int64_t* n_active, int64_t* n_ghost, int64_t* n_tube) {
@@ -89,7 +102,8 @@ cpm_status cpm_apply(const cpm_band* band, const double* c, const void* x, void*
                      int transpose, void* stream) {
   if (!band || !c || !x || !y) return fail(CPM_ERR_ARG, "null argument");
   if (nrhs < 1) return fail(CPM_ERR_ARG, "nrhs must be >= 1");
-  if (x == y) return fail(CPM_ERR_ARG, "x and y must not overlap");
+  if (ranges_overlap(x, y, (size_t)nrhs * (size_t)band->nA * (dtype == CPM_F64 ? 8u : 4u)))
+    return fail(CPM_ERR_ARG, "x and y must not overlap");
   for (int q = 0; q < nrhs; ++q)
     if (!std::isfinite(c[q])) return fail(CPM_ERR_NAN, "shift c[%d] is not finite", q);
   return apply_op(band, c, x, y, dtype, nrhs, transpose ? 1 : 0, as_stream(stream));
@@ -104,19 +118,34 @@ cpm_status oras_setup(const cpm_band* band, const oras_params* prm, double c, vo
     return fail(CPM_ERR_ARG, "Robin parameters must be >= 0 (infinity allowed)");
   if (prm->store != CPM_F32 && prm->store != CPM_BF16 && prm->store != CPM_F64)
     return fail(CPM_ERR_ARG, "store must be CPM_F64, CPM_F32 or CPM_BF16");
-  if (prm->order != 1 && prm->order != 2) return fail(CPM_ERR_ARG, "order must be 1 (distance) or 2 (shells)");
+  if (prm->order < 0 || prm->order > 2)
+    return fail(CPM_ERR_ARG, "order must be 0 (by degree), 1 (distance) or 2 (shells)");
   if (!std::isfinite(c)) return fail(CPM_ERR_NAN, "shift c is not finite");
   g_err[0] = 0;
-  return oras_build(band, prm, c, as_stream(stream), out);
+  oras_params q = *prm;
+  if (q.order == 0) q.order = band->p == 3 ? 2 : 1;  // the order measured best for each degree
+  return oras_build(band, &q, c, as_stream(stream), out);
 }
 
 cpm_status oras_apply(const oras_pc* pc, const void* r, void* z, cpm_dtype dtype, int nrhs, int transpose,
                       void* stream) {
   if (!pc || !r || !z) return fail(CPM_ERR_ARG, "null argument");
-  if (r == z) return fail(CPM_ERR_ARG, "r and z must not overlap");
   if (nrhs < 1) return fail(CPM_ERR_ARG, "nrhs must be >= 1");
   if (dtype != CPM_F64 && dtype != CPM_F32) return fail(CPM_ERR_ARG, "oras_apply supports CPM_F64 and CPM_F32");
+  if (ranges_overlap(r, z, (size_t)nrhs * (size_t)pc->nA * (dtype == CPM_F64 ? 8u : 4u)))
+    return fail(CPM_ERR_ARG, "r and z must not overlap");
   return oras_run(pc, r, z, dtype, nrhs, transpose ? 1 : 0, as_stream(stream));
+}
+
+cpm_status oras_set_tuning(oras_pc* pc, const oras_tuning* t) {
+  if (!pc || !t) return fail(CPM_ERR_ARG, "null argument");
+  if (t->xplace != 0 && t->xplace != 1) return fail(CPM_ERR_ARG, "xplace must be 0 or 1");
+  if (t->probe_timeout != 0 && t->probe_timeout != 1) return fail(CPM_ERR_ARG, "probe_timeout must be 0 or 1");
+  if (t->wait_polls < 0 || t->wait_polls > 0xffffffffll) return fail(CPM_ERR_ARG, "wait_polls must be in [0, 2^32)");
+  pc->xplace = t->xplace;
+  pc->probe_timeout = t->probe_timeout;
+  pc->wait_polls = t->wait_polls;
+  return CPM_OK;
 }
 
 cpm_status oras_info(const oras_pc* pc, int32_t* nparts, int64_t* total_rows, int64_t* total_nnz,

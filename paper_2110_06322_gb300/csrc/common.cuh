@@ -17,6 +17,7 @@ namespace cpm {
 // every kernel launch of the library goes through KL(...) so that callers can
 // count the kernels of a region (cpm_kernel_launches)
 extern std::atomic<long long> g_launches;
+extern std::atomic<long long> g_allocs;  // device allocations made (cpm_device_allocations)
 inline void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 #define KL(...) ::cpm::count_launch(), __VA_ARGS__
 
@@ -47,6 +48,7 @@ cpm_status dalloc(T** p, size_t n, cudaStream_t s) {
   *p = nullptr;
   if (n == 0) n = 1;
   keep_pool_memory();
+  g_allocs.fetch_add(1, std::memory_order_relaxed);
   cudaError_t e = cudaMallocAsync((void**)p, n * sizeof(T), s);
   if (e == cudaErrorMemoryAllocation) {
     cudaGetLastError();
@@ -60,6 +62,12 @@ template <typename T>
 void dfree(T*& p, cudaStream_t s) {
   if (p) cudaFreeAsync((void*)p, s);
   p = nullptr;
+}
+
+// two buffers of `bytes` bytes each, starting at a and b, share a byte
+inline bool ranges_overlap(const void* a, const void* b, size_t bytes) {
+  const uintptr_t pa = (uintptr_t)a, pb = (uintptr_t)b;
+  return bytes > 0 && pa < pb + bytes && pb < pa + bytes;
 }
 
 inline int grid_for(int64_t n, int block, int64_t cap = 152 * 64) {
@@ -133,6 +141,12 @@ struct cpm_band {
   uint32_t* tent = nullptr;      // packed row * 64 + position
   double* tw64 = nullptr;        // tensor weight of each entry, (w_u w_v) w_w in FP64
   float* tw32 = nullptr;         // the same rounded to FP32
+  // E rows grouped by interpolation cube (FP32 apply): rows sharing a cube
+  // base are consecutive in grow; a work item is at most EGROUP_MAX of them
+  int64_t nitem = 0;
+  int32_t* gitem = nullptr;      // [nitem][2] {first position << 4 | (rows - 1), base node (canonical rank)}
+  int32_t* grow = nullptr;       // [nR] E rows in cube-base order (ascending row within a cube)
+  float* gs32 = nullptr;         // [nR][3] FP32 offsets of those rows, same order
   // scratch for the operator apply
   void* wbuf = nullptr;          // [nR] E x values (FP64 room)
   size_t wbuf_bytes = 0;

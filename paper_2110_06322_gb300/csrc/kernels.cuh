@@ -23,8 +23,13 @@ cpm_status apply_op(const cpm_band* B, const double* c, const void* x, void* y, 
 // E x for all rows (into B->wbuf) followed by the stencil; exposed so that
 // the solver can reuse it with device-side c.
 cpm_status build_transpose_map(cpm_band* B, cudaStream_t s);
+// group the E rows by interpolation cube for the FP32 apply (band build)
+cpm_status build_erow_groups(cpm_band* B, cudaStream_t s);
 cpm_status apply_op_scratch(const cpm_band* B, const double* c, const void* x, void* y, cpm_dtype dt, int nrhs,
                             void* scratch, cudaStream_t s);
+
+// noalloc.cu: commit the fixed scratch of cpm_apply_noalloc on the current device
+cpm_status noalloc_prepare();
 
 // batch.cu: lockstep GMRES over many systems
 cpm_status solve_batch(int nprob, const cpm_band* const* bands, const oras_pc* const* pcs, const double* c,

@@ -7,16 +7,19 @@
 // pool that has reserved the device, so a foreign cudaMalloc fails or
 // fragments it), and latency-bounded loops in which an allocation may block
 // or synchronise.  This entry point uses instead one fixed scratch array that
-// lives in this file as a static __device__ variable: every GPU that loads
-// the library holds it (16 MiB) until the process exits.
+// lives in this file as a static __device__ variable: every GPU on which a
+// band has been built holds it (16 MiB) until the process exits.
 //
 // Host code cannot use the array's name as a device address (on the host it
 // names a stand-in object), so the device address is looked up once per
-// device with cudaGetSymbolAddress, with that device current, on the first
-// call made on that device; that first call should therefore come before any
-// stream capture.  All calls share the array: calls whose kernels overlap on
-// the GPU (two streams, two threads) race on it.  Nothing in the scratch needs
-// to start at zero -- every call writes each entry it reads.
+// device with cudaGetSymbolAddress, with that device current.  Under CUDA's
+// lazy module loading that lookup is also what loads this file's module and
+// so commits the 16 MiB on the device; cpm_band_build therefore does it
+// (noalloc_prepare) when it builds a band, while the caller is still in its
+// allocating phase, and the entry point only reads the cached address.  All
+// calls share the array: calls whose kernels overlap on the GPU (two
+// streams, two threads) race on it.  Nothing in the scratch needs to start
+// at zero -- every call writes each entry it reads.
 #include <mutex>
 
 #include "kernels.cuh"
@@ -47,6 +50,16 @@ cpm_status scratch_address(int dev, void** out) {
 }
 
 }  // namespace
+
+// Commit the scratch array on the current device and cache its address
+// (called by cpm_band_build for the band's device).
+cpm_status noalloc_prepare() {
+  int dev = 0;
+  CPM_CUDA(cudaGetDevice(&dev));
+  void* p = nullptr;
+  return scratch_address(dev, &p);
+}
+
 }  // namespace cpm
 
 using namespace cpm;
@@ -55,8 +68,9 @@ extern "C" cpm_status cpm_apply_noalloc(const cpm_band* band, const double* c, c
                                         cpm_dtype dtype, int nrhs, void* stream) {
   if (!band || !c || !x || !y) return fail(CPM_ERR_ARG, "null argument");
   if (nrhs < 1) return fail(CPM_ERR_ARG, "nrhs must be >= 1");
-  if (x == y) return fail(CPM_ERR_ARG, "x and y must not overlap");
   if (dtype != CPM_F64 && dtype != CPM_F32) return fail(CPM_ERR_ARG, "dtype must be CPM_F64 or CPM_F32");
+  if (ranges_overlap(x, y, (size_t)nrhs * (size_t)band->nA * (dtype == CPM_F64 ? 8u : 4u)))
+    return fail(CPM_ERR_ARG, "x and y must not overlap");
   for (int q = 0; q < nrhs; ++q)
     if (!(c[q] == c[q]) || c[q] - c[q] != 0.0) return fail(CPM_ERR_NAN, "shift c[%d] is not finite", q);
   int dev = 0;

@@ -73,6 +73,10 @@ struct oras_pc {
   // level-packed factors: [0] FP64, [1] store type, [2] transposed FP64, [3] transposed FP32
   PackedFactors packed[4];
   int* err = nullptr;         // device flag: a bounded wait of the apply ran out
+  // run-time settings of the apply (oras_set_tuning)
+  int xplace = 0;             // 0 local vector in shared memory when it fits, 1 always a global slice
+  int probe_timeout = 0;      // failure-path test: the first chunk wait can only run out
+  int64_t wait_polls = 0;     // polls of each consumer-side wait (0: the default)
 };
 
 namespace cpm {
@@ -86,6 +90,9 @@ cpm_status pack_factors(oras_pc* P, int transposed, const cpm_dtype* vt, PackedF
                         cudaStream_t s);
 void packed_free(PackedFactors& pf, cudaStream_t s);
 void oras_destroy(oras_pc* P, cudaStream_t s);
+// Read and clear the preconditioner's timeout flag (synchronises the stream):
+// CPM_ERR_TIMEOUT if a bounded wait of an apply since the last check ran out.
+cpm_status oras_take_error(const oras_pc* P, cudaStream_t s);
 cpm_status solve_run(const cpm_band* B, const oras_pc* P, double c, const double* f, double* u,
                      const cpm_solve_params* prm, cpm_solve_info* info, int transpose, cudaStream_t s);
 }  // namespace cpm

@@ -23,8 +23,11 @@
 // 32 / SW_LPR rows share each shuffle) and meet at
 // one CTA barrier per chunk, which is also the level barrier.  The local
 // vector lives in shared memory when it fits, else in a global slice.  Every
-// mbarrier wait is bounded; a wait that runs out sets an error flag, the CTA
-// drains its copies in flight (bounded) and returns.
+// mbarrier wait is bounded.  A wait that runs out sets an error flag; the
+// producer then stops issuing, and before the CTA returns it waits (bounded)
+// for the last copy it issued into each ring stage -- the only copies that
+// can still be in flight, since every earlier copy into a stage was waited
+// for by the consumers before the stage was refilled.
 #include <algorithm>
 #include <type_traits>
 #include <vector>
@@ -405,6 +408,8 @@ struct PkArgs {
   int transpose;
   int64_t nA, nloc;
   int* err;
+  uint32_t wait_limit;  // polls of each consumer-side wait before it gives up
+  int probe;            // failure-path test: the first chunk wait waits on a barrier nothing completes
 };
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -413,6 +418,17 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // barrier among the consumer warps only (named barrier 1)
 __device__ __forceinline__ void consumer_sync() {
   asm volatile("bar.sync 1, %0;" ::"n"(PK_WARPS * 32) : "memory");
+}
+// the same barrier, returning the OR of every consumer thread's v: all
+// consumers get the same answer, so they stop at the same chunk
+__device__ __forceinline__ bool consumer_sync_or(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "n"(PK_WARPS * 32)
+      : "memory");
+  return r != 0;
 }
 
 // partial dot product of one packed row with the local vector: lane `sub`
@@ -439,8 +455,9 @@ template <typename T, typename V, bool SMEMX>
 __global__ void __launch_bounds__((PK_WARPS + 1) * 32, 2)
     k_schwarz_pk(PkArgs A, const T* __restrict__ r, T* __restrict__ z, T* xglob) {
   extern __shared__ __align__(128) unsigned char pk_smem[];
-  __shared__ uint64_t full[NSTAGE], empty[NSTAGE];
+  __shared__ uint64_t full[NSTAGE], empty[NSTAGE], probe_bar;
   __shared__ int abort_flag;
+  int64_t issued = 0;  // chunks the producer lane has issued (used by its drain)
   const int j = A.order[blockIdx.x], rhs = blockIdx.y;
   const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
   const bool producer = wid == PK_WARPS;
@@ -459,6 +476,7 @@ __global__ void __launch_bounds__((PK_WARPS + 1) * 32, 2)
       mbar_init(&full[q], 1);
       mbar_init(&empty[q], 1);
     }
+    mbar_init(&probe_bar, 1);  // never arrived on: a wait on it can only run out
     fence_mbar_init();
   }
   __syncthreads();
@@ -485,6 +503,7 @@ __global__ void __launch_bounds__((PK_WARPS + 1) * 32, 2)
         mbar_expect_tx(&full[st], bytes);
         bulk_g2s(ring + st * CHUNK_BYTES, A.data + off, bytes, &full[st]);
         off += bytes;
+        ++issued;
       }
     }
   } else {
@@ -495,10 +514,12 @@ __global__ void __launch_bounds__((PK_WARPS + 1) * 32, 2)
     consumer_sync();
     for (int64_t c = 0; c < nch; ++c) {
       const int st = (int)(c % NSTAGE);
-      const uint32_t par = (uint32_t)((c / NSTAGE) & 1);
+      const bool probe = A.probe && c == 0;
+      uint64_t* bar = probe ? &probe_bar : &full[st];
+      const uint32_t par = probe ? 0u : (uint32_t)((c / NSTAGE) & 1);
       unsigned polls = 0;
-      while (!mbar_try_wait(&full[st], par)) {
-        if (++polls > WAIT_LIMIT) {
+      while (!mbar_try_wait(bar, par)) {
+        if (++polls > A.wait_limit) {
           abort_flag = 1;
           break;
         }
@@ -508,7 +529,9 @@ __global__ void __launch_bounds__((PK_WARPS + 1) * 32, 2)
       const int4* hdr = reinterpret_cast<const int4*>(buf + 16);
       const uint16_t* cols = reinterpret_cast<const uint16_t*>(buf + 16 + 16 * (int64_t)ch.x);
       const V* vals = reinterpret_cast<const V*>(buf + 16 + 16 * (int64_t)ch.x + pad16(2 * (int64_t)ch.y));
-      if (!abort_flag) {
+      // skip the chunk when this warp saw the abort (decided per warp, so
+      // that either all lanes or none reach the shuffles below)
+      if (!__any_sync(0xffffffffu, *(volatile int*)&abort_flag != 0)) {
         constexpr int LPR = SW_LPR, RPW = 32 / LPR;  // lanes per row, rows per warp
         const int e0 = ch.z ? 1 : 0, sub = lane & (LPR - 1);
         // rows rb + RPW * wid + lane / LPR; the loop is warp-uniform so that
@@ -531,19 +554,30 @@ __global__ void __launch_bounds__((PK_WARPS + 1) * 32, 2)
           }
         }
       }
-      consumer_sync();  // level barrier; the stage is free again
+      // level barrier (the stage is free again) and one abort decision for
+      // all consumers: the producer may set the flag at any time
+      const bool stop = consumer_sync_or(*(volatile int*)&abort_flag != 0);
       if (tid == 0) mbar_arrive(&empty[st]);
-      if (abort_flag) break;
+      if (stop) {
+        abort_flag = 1;
+        break;
+      }
     }
   }
   __syncthreads();
   if (abort_flag) {
     if (tid == 0) atomicExch(A.err, CPM_ERR_TIMEOUT);
-    // drain copies in flight (bounded) before the shared memory goes away
+    // Drain before the shared memory goes away.  Chunk c went into stage
+    // c % NSTAGE and completes phase c / NSTAGE of full[stage].  Only the
+    // last chunk issued into each stage can still be in flight (the producer
+    // refills a stage only after the consumers released it, and they stop at
+    // the first wait that runs out), so wait for that chunk's phase.
     if (producer && lane == 0)
-      for (int q = 0; q < NSTAGE; ++q) {
+      for (int q = 0; q < NSTAGE && q < issued; ++q) {
+        const int64_t last = q + (int64_t)NSTAGE * ((issued - 1 - q) / NSTAGE);
+        const uint32_t par = (uint32_t)((last / NSTAGE) & 1);
         unsigned polls = 0;
-        while (!mbar_try_wait(&full[q], 0) && !mbar_try_wait(&full[q], 1) && ++polls < WAIT_LIMIT) {
+        while (!mbar_try_wait(&full[q], par) && ++polls < WAIT_LIMIT) {
         }
       }
     return;
@@ -616,6 +650,28 @@ void packed_free(PackedFactors& pf, cudaStream_t s) {
   pf.bytes = 0;
 }
 
+// Largest dynamic shared memory a Schwarz CTA asks for: the ring and the
+// chunk-size table, plus the local vector when it lives in shared memory
+// (at most 113 KB in total, so that two CTAs fit on one SM).
+constexpr size_t PK_SMEM_MAX = 113 * 1024;
+
+// Raise the kernels' dynamic shared-memory limit once per device (the
+// attribute is a ceiling; each launch asks for what it needs).
+template <typename T, typename V>
+static cpm_status allow_pk_smem(cudaStream_t) {
+  static std::atomic<unsigned long long> done{0};
+  int dev = 0;
+  CPM_CUDA(cudaGetDevice(&dev));
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (done.load() & bit) return CPM_OK;
+  CPM_CUDA(cudaFuncSetAttribute(k_schwarz_pk<T, V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)PK_SMEM_MAX));
+  CPM_CUDA(cudaFuncSetAttribute(k_schwarz_pk<T, V, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)PK_SMEM_MAX));
+  done.fetch_or(bit);
+  return CPM_OK;
+}
+
 template <typename T, typename V>
 static cpm_status run_pk(const oras_pc* P, const PackedFactors& pf, const T* r, T* z, int nrhs, int transpose,
                          cudaStream_t s) {
@@ -633,26 +689,28 @@ static cpm_status run_pk(const oras_pc* P, const PackedFactors& pf, const T* r, 
   A.order = pf.order;
   A.csz = pf.csz;
   A.csz_bytes = pad16(2 * pf.max_chunks);
+  A.wait_limit = P->wait_polls > 0 ? (uint32_t)std::min<int64_t>(P->wait_polls, 0xffffffffll) : WAIT_LIMIT;
+  A.probe = P->probe_timeout;
   const size_t ring = (size_t)NSTAGE * CHUNK_BYTES + A.csz_bytes;
   const size_t xsb = (size_t)P->max_rows * sizeof(T);
-  const bool smemx = ring + xsb <= 113 * 1024;  // two CTAs per SM
+  // local vector in shared memory when it fits beside the ring with two CTAs
+  // per SM, unless the caller asked for the global slice
+  const bool smemx = P->xplace == 0 && ring + xsb <= 113 * 1024;
+  const size_t sm = smemx ? ring + xsb : ring;
+  if (sm > PK_SMEM_MAX) return fail(CPM_ERR_ARG, "Schwarz apply needs %zu bytes of shared memory", sm);
+  CPM_TRY((allow_pk_smem<T, V>(s)));
   T* xloc = nullptr;
   if (!smemx || transpose) CPM_TRY(dalloc(&xloc, (size_t)nrhs * P->nloc, s));
   for (int r0 = 0; r0 < nrhs; r0 += 65535) {
     const int nr = nrhs - r0 < 65535 ? nrhs - r0 : 65535;
     dim3 g(P->np, nr);
     T* xl = xloc ? xloc + (int64_t)r0 * P->nloc : nullptr;
-    if (smemx) {
-      const size_t sm = ring + xsb;
-      CPM_CUDA(cudaFuncSetAttribute(k_schwarz_pk<T, V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      KL(k_schwarz_pk<T, V, true><<<g, (PK_WARPS + 1) * 32, sm, s>>>(A, r + (int64_t)r0 * P->nA, z + (int64_t)r0 * P->nA,
-                                                               xl));
-    } else {
-      CPM_CUDA(cudaFuncSetAttribute(k_schwarz_pk<T, V, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)ring));
-      KL(k_schwarz_pk<T, V, false><<<g, (PK_WARPS + 1) * 32, ring, s>>>(A, r + (int64_t)r0 * P->nA,
-                                                                  z + (int64_t)r0 * P->nA, xl));
-    }
+    if (smemx)
+      KL(k_schwarz_pk<T, V, true><<<g, (PK_WARPS + 1) * 32, sm, s>>>(A, r + (int64_t)r0 * P->nA,
+                                                                   z + (int64_t)r0 * P->nA, xl));
+    else
+      KL(k_schwarz_pk<T, V, false><<<g, (PK_WARPS + 1) * 32, sm, s>>>(A, r + (int64_t)r0 * P->nA,
+                                                                    z + (int64_t)r0 * P->nA, xl));
     if (transpose) {
       dim3 g2(grid_for(P->nA, 256), nr);
       KL(k_gather_T2<T><<<g2, 256, 0, s>>>(P->nA, P->nloc, P->mcnt, P->mloc, xl, z + (int64_t)r0 * P->nA));
@@ -662,6 +720,17 @@ static cpm_status run_pk(const oras_pc* P, const PackedFactors& pf, const T* r, 
   dfree(xloc, s);
   if (e != cudaSuccess) return cuda_fail(e, "packed Schwarz kernels", __FILE__, __LINE__);
   return CPM_OK;
+}
+
+cpm_status oras_take_error(const oras_pc* P, cudaStream_t s) {
+  if (!P) return CPM_OK;
+  int herr = 0;
+  CPM_CUDA(cudaMemcpyAsync(&herr, P->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CPM_CUDA(cudaStreamSynchronize(s));
+  if (!herr) return CPM_OK;
+  CPM_CUDA(cudaMemsetAsync(P->err, 0, sizeof(int), s));
+  CPM_CUDA(cudaStreamSynchronize(s));
+  return fail(CPM_ERR_TIMEOUT, "a bounded wait in the Schwarz apply ran out");
 }
 
 cpm_status oras_run(const oras_pc* Pc, const void* r, void* z, cpm_dtype dt, int nrhs, int transpose, cudaStream_t s) {

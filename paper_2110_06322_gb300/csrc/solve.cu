@@ -158,6 +158,20 @@ __global__ void k_axpy(const double* __restrict__ z, double* x, int64_t n) {  //
     x[i] += z[i];
 }
 
+// x += sum_t y[t] Z_t with Z_t = Z + t ld in FP32 (the preconditioned basis
+// vectors of a flexible cycle), accumulated in FP64 in a fixed order
+__global__ void k_flex_update(const float* __restrict__ Z, int64_t ld, int k, const double* __restrict__ y, double* x,
+                              int64_t n) {
+  __shared__ double ys[256];
+  for (int t = threadIdx.x; t < k; t += blockDim.x) ys[t] = y[t];
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0;
+    for (int t = 0; t < k; ++t) acc += ys[t] * (double)Z[t * ld + i];
+    x[i] += acc;
+  }
+}
+
 __global__ void k_d2f(const double* __restrict__ a, float* b, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     b[i] = (float)a[i];
@@ -223,6 +237,7 @@ struct Work {
   int m = 0;
   double *V = nullptr, *w = nullptr, *z = nullptr, *t = nullptr, *r = nullptr;
   float *v32 = nullptr, *z32 = nullptr, *w32 = nullptr;
+  float* Z32 = nullptr;  // m x n: preconditioned basis vectors of a flexible (mixed-precision) cycle
   double *H = nullptr, *hc = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr, *ny = nullptr;
   double *partial = nullptr, *scal = nullptr;  // partial: (32 + 1) x RED_BLOCKS
   double* pub = nullptr;  // pinned host: two slots of {|g_{j+1}|, h_{j+1,j}, 1/h_{j+1,j}} at 0 and 4
@@ -238,6 +253,7 @@ struct Work {
     if (f32) {
       CPM_TRY(dalloc(&v32, n, s));
       CPM_TRY(dalloc(&z32, n, s));
+      CPM_TRY(dalloc(&Z32, (size_t)m * n, s));
       CPM_TRY(dalloc(&w32, n, s));
     }
     CPM_TRY(dalloc(&H, (size_t)(m + 1) * m, s));
@@ -257,6 +273,7 @@ struct Work {
     for (double** p : {&V, &w, &z, &t, &r, &H, &hc, &cs, &sn, &g, &y, &ny, &partial, &scal}) dfree(*p, s);
     dfree(v32, s);
     dfree(z32, s);
+    dfree(Z32, s);
     dfree(w32, s);
     if (pub) cudaFreeHost(pub);
     pub = nullptr;
@@ -297,6 +314,10 @@ struct Ops {
   int transpose;
   int f32;  // operator and preconditioner in FP32
   Timing* tm;
+  // flexible cycle (FP32 applies with a preconditioner): z_j = P v_j is kept
+  // (in FP32, as computed) and the cycle ends with x += Z y, so the update is
+  // made of exactly the vectors the Arnoldi relation M Z = V H was built from
+  bool flex() const { return f32 && P; }
 };
 
 const int GB = RED_BLOCKS;
@@ -337,19 +358,21 @@ cpm_status op_P(const Ops& o, const double* v, double* out, Work& W, cudaStream_
   return CPM_OK;
 }
 
-// w = M P v.  In FP32 the preconditioned vector stays FP32 between the two
-// applies (its FP64 copy would round back to the same FP32 values).
-cpm_status op_MP(const Ops& o, const double* v, double* w, Work& W, cudaStream_t s) {
-  if (!o.f32 || !o.P) {
+// w = M P v_j.  In FP32 the preconditioned vector stays FP32 between the two
+// applies (its FP64 copy would round back to the same FP32 values) and is
+// kept as column j of the flexible basis Z.
+cpm_status op_MP(const Ops& o, const double* v, double* w, int j, Work& W, cudaStream_t s) {
+  if (!o.flex()) {
     CPM_TRY(op_P(o, v, W.z, W, s));
     return op_M(o, W.z, w, W, s);
   }
+  float* zj = W.Z32 + (int64_t)j * W.n;
   KL(k_d2f<<<grid_for(W.n, 256), 256, 0, s>>>(v, W.v32, W.n));
   o.tm->start(s);
-  CPM_TRY(oras_run(o.P, W.v32, W.z32, CPM_F32, 1, o.transpose, s));
+  CPM_TRY(oras_run(o.P, W.v32, zj, CPM_F32, 1, o.transpose, s));
   o.tm->stop(s, true);
   o.tm->start(s);
-  CPM_TRY(apply_op(o.B, &o.c, W.z32, W.w32, CPM_F32, 1, o.transpose, s));
+  CPM_TRY(apply_op(o.B, &o.c, zj, W.w32, CPM_F32, 1, o.transpose, s));
   o.tm->stop(s, false);
   KL(k_f2d<<<grid_for(W.n, 256), 256, 0, s>>>(W.w32, w, W.n));
   return CPM_OK;
@@ -485,6 +508,13 @@ cpm_status gmres(const Ops& o, const double* f, double* x, int m, int maxit, dou
     double b2 = 0;
     CPM_CUDA(cudaMemcpyAsync(&b2, W.scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
     CPM_CUDA(cudaStreamSynchronize(s));
+    if (o.P) {  // a Schwarz apply of the last cycle ran out of a bounded wait: its output is not usable
+      const cpm_status te = oras_take_error(o.P, s);
+      if (te != CPM_OK) {
+        out.status = te;
+        return te;
+      }
+    }
     const double beta = std::sqrt(b2);
     out.relres = beta / fn;
     if (!std::isfinite(beta)) {
@@ -526,7 +556,7 @@ cpm_status gmres(const Ops& o, const double* f, double* x, int m, int maxit, dou
     bool stop = false;
     for (int j = 0; j < jmax && !stop; ++j) {
       double* vj = W.V + (int64_t)j * n;
-      CPM_TRY(op_MP(o, vj, W.w, W, s));
+      CPM_TRY(op_MP(o, vj, W.w, j, W, s));
       CPM_TRY(gram_schmidt(j, reorth, W, s));
       KL(k_givens<<<1, 1, 0, s>>>(W.H, m, W.hc, W.cs, W.sn, W.g, j, W.scal + 2));
       CPM_CUDA(cudaMemcpyAsync(W.pub + 4 * (j & 1), W.scal + 2, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -537,8 +567,13 @@ cpm_status gmres(const Ops& o, const double* f, double* x, int m, int maxit, dou
     }
     if (!stop && jmax > 0) CPM_TRY(check(jmax - 1, stop));
     out.iters += k;
-    // x += P (V y)
     KL(k_trisolve<<<1, 1, 0, s>>>(W.H, m, W.g, k, W.y));
+    if (o.flex()) {  // x += Z y
+      KL(k_flex_update<<<G, 256, 0, s>>>(W.Z32, n, k, W.y, x, n));
+      CPM_CUDA(cudaGetLastError());
+      continue;
+    }
+    // x += P (V y)
     CPM_CUDA(cudaMemsetAsync(W.t, 0, n * sizeof(double), s));
     KL(k_negate<<<1, 256, 0, s>>>(W.y, W.ny, k));
     const int cs = gs_chunk(k);
@@ -601,6 +636,13 @@ cpm_status solve_run(const cpm_band* B, const oras_pc* P, double c, const double
       cudaMemcpyAsync(&r2, W.scal + 5, sizeof(double), cudaMemcpyDeviceToHost, s);
       cudaStreamSynchronize(s);
       out.relres = fn > 0 ? std::sqrt(r2) / fn : 0.0;
+      if (P) {
+        st = oras_take_error(P, s);
+        if (st != CPM_OK) {
+          out.status = st;
+          break;
+        }
+      }
       if (!std::isfinite(out.relres)) {
         st = fail(CPM_ERR_NAN, "residual became NaN or Inf");
         out.status = CPM_ERR_NAN;
@@ -616,7 +658,12 @@ cpm_status solve_run(const cpm_band* B, const oras_pc* P, double c, const double
       }
       cudaMemsetAsync(d, 0, n * sizeof(double), s);
       GmresOut in;
-      st = gmres(o32, r, d, prm->restart, prm->maxit - out.iters, inner, prm->reorth, W, in, s, true);
+      // the inner cycle may stop once its estimate is well below what the
+      // outer tolerance still asks for (half of it: FP32 applies make the
+      // estimate and the FP64 residual differ slightly)
+      const double rn = std::sqrt(r2);
+      const double tol_in = std::max(inner, rn > 0 ? 0.5 * prm->rtol * fn / rn : inner);
+      st = gmres(o32, r, d, prm->restart, prm->maxit - out.iters, tol_in, prm->reorth, W, in, s, true);
       out.iters += in.iters;
       out.cycles += in.cycles;
       info->ir_steps++;
@@ -628,9 +675,10 @@ cpm_status solve_run(const cpm_band* B, const oras_pc* P, double c, const double
   }
   cudaError_t e = cudaStreamSynchronize(s);
   if (P && e == cudaSuccess) {
-    int herr = 0;
-    cudaMemcpy(&herr, P->err, sizeof(int), cudaMemcpyDeviceToHost);
-    if (herr && st == CPM_OK) st = fail(CPM_ERR_TIMEOUT, "a bounded wait in the Schwarz apply ran out");
+    // a timed-out apply makes every later result meaningless: it takes
+    // precedence over whatever the iteration concluded from it
+    const cpm_status te = oras_take_error(P, s);
+    if (te != CPM_OK) st = te;
   }
   W.release(s);
   cudaStreamSynchronize(s);

@@ -66,19 +66,24 @@ def surface_params(kind: int, center=(0.0, 0.0, 0.0), a: float = 1.0, b: float =
     return (float(center[0]), float(center[1]), float(center[2]), float(a), float(b))
 
 
+# Each workload: surface, spacing h, degree p, shift c, right-hand side, Schwarz
+# preconditioner (parts, overlap, Robin or not, ILU(0) local order) and GMRES
+# settings; solve_rtol is the relative residual the benchmark solves to.
 WORKLOADS = {
     "sphere_h0.1": dict(kind=SPHERE, params=surface_params(SPHERE, a=1.0), h=0.1, p=3, c=1.0,
                         rhs="y32", nparts=8, overlap=2, robin=False, restart=30, rtol=1e-10),
     "torus_h0.004": dict(kind=TORUS, params=surface_params(TORUS, a=1.0, b=0.4), h=0.004, p=3, c=10.0,
                          rhs="modes", seed=2, nparts=512, overlap=2, robin=False, alpha=4.0, alpha_cross=20.0,
-                         restart=30, rtol=1e-8),
+                         restart=30, rtol=1e-8, solve_rtol=1e-8, order=2),
     "torus_h0.0125": dict(kind=TORUS, params=surface_params(TORUS, a=1.0, b=0.4), h=0.0125, p=3, c=10.0,
-                          rhs="modes", seed=2, nparts=64, overlap=2, robin=False, restart=30, rtol=1e-8),
+                          rhs="modes", seed=2, nparts=64, overlap=2, robin=False, restart=30, rtol=1e-8,
+                          solve_rtol=1e-8, order=2),
     "torus_h0.025": dict(kind=TORUS, params=surface_params(TORUS, a=1.0, b=0.4), h=0.025, p=3, c=10.0,
-                         rhs="modes", seed=2, nparts=16, overlap=2, robin=False, restart=30, rtol=1e-8),
+                         rhs="modes", seed=2, nparts=16, overlap=2, robin=False, restart=30, rtol=1e-8,
+                         solve_rtol=1e-8, order=2),
     "torus_h0.002": dict(kind=TORUS, params=surface_params(TORUS, a=1.0, b=0.4), h=0.002, p=3, c=10.0,
                          rhs="modes", seed=3, nparts=512, overlap=2, robin=False, alpha=4.0, alpha_cross=20.0,
-                         restart=30, rtol=1e-8),
+                         restart=30, rtol=1e-8, solve_rtol=1e-8, order=2),
     # differentiable Schnakenberg run (eq. schnack): D = (1e-3, 1e-1), dt = 0.01, 500 steps, state
     # checkpoints every 25 steps; initial state (u*, v*) (1 + 0.01 U[-1, 1]) from seed 7 (u) and 8 (v)
     "schnakenberg_torus_h0.005": dict(kind=TORUS, params=surface_params(TORUS, a=1.0, b=0.4), h=0.005, p=3,

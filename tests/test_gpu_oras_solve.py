@@ -53,11 +53,12 @@ def _cuda(x):
     return torch.from_numpy(np.ascontiguousarray(x)).cuda()
 
 
+@pytest.mark.parametrize("order", [1, 2])
 @pytest.mark.parametrize("nparts,overlap", [(1, 0), (8, 2), (13, 1), (64, 2), (64, 3)])
-def test_partition_and_local_order_identical(cpm, oracle_mod, torus005, nparts, overlap):
+def test_partition_and_local_order_identical(cpm, oracle_mod, torus005, nparts, overlap, order):
     B, O, M = torus005
-    P = cpm.Schwarz(B, 10.0, nparts, overlap)
-    OP = oracle_mod.ORAS(O, M, nparts, overlap)
+    P = cpm.Schwarz(B, 10.0, nparts, overlap, order=order)
+    OP = oracle_mod.ORAS(O, M, nparts, overlap, order=order)
     part, sptr, nodes = [t.cpu().numpy() for t in P.export()]
     assert np.array_equal(part, OP.partition())
     for j in range(nparts):
@@ -67,8 +68,8 @@ def test_partition_and_local_order_identical(cpm, oracle_mod, torus005, nparts, 
 @pytest.mark.parametrize("robin", [False, True])
 def test_schwarz_apply_matches_oracle(cpm, oracle_mod, torus005, robin):
     B, O, M = torus005
-    P = cpm.Schwarz(B, 10.0, 16, 2, robin=robin)
-    OP = oracle_mod.ORAS(O, M, 16, 2, robin=robin)
+    P = cpm.Schwarz(B, 10.0, 16, 2, robin=robin)  # default local order: shells and colours for p = 3
+    OP = oracle_mod.ORAS(O, M, 16, 2, robin=robin, order=oracle_mod.ORAS.LOCAL_SHELLS)
     r = inputs.gaussian_vector(5, B.n_active)
     want = OP.apply(r)
     got = P.apply(_cuda(r)).cpu().numpy()
@@ -83,7 +84,7 @@ def test_schwarz_apply_matches_oracle(cpm, oracle_mod, torus005, robin):
 def test_schwarz_several_rhs(cpm, oracle_mod, sphere01):
     B, O, M = sphere01
     P = cpm.Schwarz(B, 1.0, 8, 2, robin=True)
-    OP = oracle_mod.ORAS(O, M, 8, 2, robin=True)
+    OP = oracle_mod.ORAS(O, M, 8, 2, robin=True, order=oracle_mod.ORAS.LOCAL_SHELLS)
     R = np.stack([inputs.gaussian_vector(60 + q, B.n_active) for q in range(3)])
     Z = P.apply(_cuda(R).reshape(-1)).cpu().numpy().reshape(3, -1)
     for q in range(3):
@@ -214,3 +215,156 @@ def test_full_size_torus_solve(cpm, oracle_mod):
     res = O.apply_rows(c, u32n, rows) - f[rows]
     assert np.abs(res).max() <= 2e-10 * np.linalg.norm(f)
     assert np.linalg.norm(un - u32n) <= 1e-6 * np.linalg.norm(u32n)
+
+
+@pytest.fixture(scope="module")
+def torus0025(cpm, oracle_mod):
+    """Torus h = 0.025 in 4 parts: subdomains of ~38k rows whose local vectors
+    do not fit in shared memory (FP64 or FP32), about 175 rows per
+    dependency level, so every level spans several factor chunks."""
+    B = cpm.Band(1, TOR, 0.025, 3)
+    O = oracle_mod.Band(1, TOR, 0.025, 3)
+    M = O.M(10.0)
+    return B, O, M, oracle_mod.ORAS(O, M, 4, 2, order=oracle_mod.ORAS.LOCAL_SHELLS)
+
+
+def _rel(got, want):
+    return np.abs(got - want).max() / np.abs(want).max()
+
+
+# BF16 factor storage rounds every stored factor entry to 8 significant bits
+# (relative error <= 2^-9); through the two triangular sweeps of ~60-entry rows
+# this bounds the apply's error at a few 1e-3 of max|z| on these bands; 2e-2
+# leaves a margin while still failing any wrong entry, level or row.
+BF16_TOL = 2e-2
+
+
+@pytest.mark.parametrize("robin", [False, True])
+def test_schwarz_global_slice_branch_matches_oracle(cpm, oracle_mod, torus005, robin):
+    """The apply with every local vector in a global-memory slice (the branch
+    large subdomains take), forced on the small torus: FP64, FP32 and BF16
+    factors, forward and transposed, RAS and the Robin reading."""
+    B, O, M = torus005
+    OP = oracle_mod.ORAS(O, M, 16, 2, robin=robin, order=oracle_mod.ORAS.LOCAL_SHELLS)
+    r = inputs.gaussian_vector(15, B.n_active)
+    want, wantT = OP.apply(r), OP.apply(r, transpose=True)
+    for store in (cpm.CPM_F32, cpm.CPM_BF16):
+        P = cpm.Schwarz(B, 10.0, 16, 2, robin=robin, store=store)
+        P.set_tuning(xplace=1)
+        assert _rel(P.apply(_cuda(r)).cpu().numpy(), want) <= 1e-12
+        assert _rel(P.apply(_cuda(r), transpose=True).cpu().numpy(), wantT) <= 1e-12
+        got32 = P.apply(_cuda(r).float()).double().cpu().numpy()
+        assert _rel(got32, want) <= (1e-4 if store == cpm.CPM_F32 else BF16_TOL)
+        gotT32 = P.apply(_cuda(r).float(), transpose=True).double().cpu().numpy()
+        assert _rel(gotT32, wantT) <= 1e-4
+        # the same preconditioner with the shared-memory branch gives the same values
+        P.set_tuning(xplace=0)
+        assert _rel(P.apply(_cuda(r)).cpu().numpy(), want) <= 1e-12
+
+
+def test_schwarz_large_subdomains_multichunk_levels(cpm, oracle_mod, torus0025):
+    """~38k-row subdomains (global-slice branch chosen by size, levels of
+    several chunks): element-wise against the oracle in FP64 and FP32,
+    forward and transposed, with two right-hand sides."""
+    B, O, M, OP = torus0025
+    P = cpm.Schwarz(B, 10.0, 4, 2, store=cpm.CPM_F32)
+    part, sptr, nodes = [t.cpu().numpy() for t in P.export()]
+    assert np.array_equal(part, OP.partition())
+    for j in range(4):
+        assert np.array_equal(nodes[sptr[j]:sptr[j + 1]], OP.sub_nodes(j))
+    R = np.stack([inputs.gaussian_vector(20 + q, B.n_active) for q in range(2)])
+    Z = P.apply(_cuda(R).reshape(-1)).cpu().numpy().reshape(2, -1)
+    ZT = P.apply(_cuda(R).reshape(-1), transpose=True).cpu().numpy().reshape(2, -1)
+    Z32 = P.apply(_cuda(R).reshape(-1).float()).double().cpu().numpy().reshape(2, -1)
+    for q in range(2):
+        want = OP.apply(R[q])
+        assert _rel(Z[q], want) <= 1e-12
+        assert _rel(Z32[q], want) <= 1e-4
+        assert _rel(ZT[q], OP.apply(R[q], transpose=True)) <= 1e-12
+
+
+def test_schwarz_timeout_is_reported_and_recovers(cpm, oracle_mod, torus005, torus005_lu):
+    """Failure path of the bounded waits, without a GPU fault: with the probe
+    on, the first chunk wait of every subdomain waits on a barrier nothing
+    completes and runs out after 1,000 polls; each CTA drains the copies it
+    issued and returns, and the solve reports CPM_ERR_TIMEOUT.  With the
+    probe off the same handles solve to the direct solution."""
+    B, O, M = torus005
+    f = inputs.gaussian_vector(16, B.n_active)
+    P = cpm.Schwarz(B, 10.0, 16, 2, store=cpm.CPM_F32)
+    for mixed in (False, True):
+        P.set_tuning(probe_timeout=1, wait_polls=1000)
+        with pytest.raises(cpm.CpmError) as e:
+            cpm.solve(B, _cuda(f), P, rtol=1e-10, maxit=200, mixed=mixed)
+        assert e.value.status == cpm.CPM_ERR_TIMEOUT
+        P.set_tuning()
+        u, info = cpm.solve(B, _cuda(f), P, rtol=1e-12, maxit=5000, mixed=mixed)
+        assert info["status"] == 0, info
+        xd = torus005_lu.solve(f)
+        assert np.linalg.norm(u.cpu().numpy() - xd) <= (1e-10 if not mixed else 1e-8) * np.linalg.norm(xd)
+
+
+@pytest.mark.parametrize("nparts,overlap", [(16, 2), (64, 2)])
+def test_shell_colour_order_matches_oracle(cpm, oracle_mod, torus005, nparts, overlap):
+    """The second local order (distance shells of width h, then lattice-parity
+    colours): subdomain lists identical to the oracle's order 2, and the
+    Schwarz apply with its factors element-wise equal (FP64 1e-12, FP32 1e-4),
+    forward and transposed."""
+    B, O, M = torus005
+    P = cpm.Schwarz(B, 10.0, nparts, overlap, order=2)
+    OP = oracle_mod.ORAS(O, M, nparts, overlap, order=oracle_mod.ORAS.LOCAL_SHELLS)
+    part, sptr, nodes = [t.cpu().numpy() for t in P.export()]
+    assert np.array_equal(part, OP.partition())
+    for j in range(nparts):
+        assert np.array_equal(nodes[sptr[j]:sptr[j + 1]], OP.sub_nodes(j))
+    assert P.max_levels == max(max(OP.depth(j, True), OP.depth(j, False)) for j in range(nparts))
+    r = inputs.gaussian_vector(17, B.n_active)
+    want = OP.apply(r)
+    assert _rel(P.apply(_cuda(r)).cpu().numpy(), want) <= 1e-12
+    assert _rel(P.apply(_cuda(r).float()).double().cpu().numpy(), want) <= 1e-4
+    assert _rel(P.apply(_cuda(r), transpose=True).cpu().numpy(), OP.apply(r, transpose=True)) <= 1e-12
+
+
+@pytest.fixture(scope="module")
+def torus005_p2(cpm, oracle_mod):
+    """Tri-quadratic interpolation (p = 2, 27-point cubes), the degree of the
+    paper's scaling runs (Section 5)."""
+    B = cpm.Band(1, TOR, 0.05, 2)
+    O = oracle_mod.Band(1, TOR, 0.05, 2)
+    M = O.M(10.0)
+    return B, O, M, sla.splu(M.to_scipy().tocsc())
+
+
+@pytest.mark.parametrize("robin", [False, True])
+def test_p2_schwarz_apply_matches_oracle(cpm, oracle_mod, torus005_p2, robin):
+    B, O, M, _ = torus005_p2
+    P = cpm.Schwarz(B, 10.0, 16, 2, robin=robin)
+    OP = oracle_mod.ORAS(O, M, 16, 2, robin=robin)
+    part, sptr, nodes = [t.cpu().numpy() for t in P.export()]
+    assert np.array_equal(part, OP.partition())
+    for j in range(16):
+        assert np.array_equal(nodes[sptr[j]:sptr[j + 1]], OP.sub_nodes(j))
+    r = inputs.gaussian_vector(31, B.n_active)
+    want = OP.apply(r)
+    assert _rel(P.apply(_cuda(r)).cpu().numpy(), want) <= 1e-12
+    assert _rel(P.apply(_cuda(r).float()).double().cpu().numpy(), want) <= 1e-4
+    assert _rel(P.apply(_cuda(r), transpose=True).cpu().numpy(), OP.apply(r, transpose=True)) <= 1e-12
+
+
+def test_p2_solves_match_direct_solve(cpm, oracle_mod, torus005_p2):
+    """p = 2: FP64 and mixed-precision forward solves and the FP64 adjoint
+    solve against the sparse LU of the oracle's M."""
+    B, O, M, lu = torus005_p2
+    f = inputs.gaussian_vector(32, B.n_active)
+    xd = lu.solve(f)
+    P = cpm.Schwarz(B, 10.0, 16, 2, store=cpm.CPM_F32)
+    u, info = cpm.solve(B, _cuda(f), P, rtol=1e-13, maxit=5000)
+    assert info["status"] == 0, info
+    assert np.linalg.norm(u.cpu().numpy() - xd) <= 1e-10 * np.linalg.norm(xd)
+    u, info = cpm.solve(B, _cuda(f), P, rtol=1e-10, maxit=5000, mixed=True)
+    assert info["status"] == 0, info
+    assert np.linalg.norm(u.cpu().numpy() - xd) <= 1e-8 * np.linalg.norm(xd)
+    lam, info = cpm.solve(B, _cuda(f), P, rtol=1e-13, maxit=5000, adjoint=True)
+    assert info["status"] == 0, info
+    ld = lu.solve(f, trans="T")
+    assert np.linalg.norm(lam.cpu().numpy() - ld) <= 1e-10 * np.linalg.norm(ld)

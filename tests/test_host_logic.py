@@ -53,10 +53,10 @@ def test_batch_arguments_are_rejected(lib):
 
 
 def test_batch_problem_draws():
-    from paper_2110_06322_gb300 import batch_bench
-    hs = [0.05, 0.025, 0.0125]
-    a = batch_bench.draw_problems(96, hs, 4)
-    b = batch_bench.draw_problems(96, hs, 4)
+    import bench
+    hs = [0.05, 0.025, 0.0125, 0.00625]
+    a = bench.draw_problems(96, hs, 4)
+    b = bench.draw_problems(96, hs, 4)
     assert a == b  # seeded
     assert [p["kind"] for p in a[:4]] == [inputs.SPHERE, inputs.TORUS, inputs.SPHERE, inputs.TORUS]
     for p in a:
@@ -68,16 +68,46 @@ def test_batch_problem_draws():
             assert 0.5 <= prm[3] <= 1.5
         else:
             assert 0.8 <= prm[3] <= 1.2 and 0.2 <= prm[4] <= 0.5
-    assert len({round(p["h"], 6) for p in a}) >= 3
+    assert len({round(p["h"], 6) for p in a}) >= 4
 
 
 def test_schnakenberg_initial_state():
-    from paper_2110_06322_gb300 import rd_gradient
+    import bench
     w = inputs.WORKLOADS["schnakenberg_torus_h0.005"]
-    u0, v0, us, vs = rd_gradient.initial_state(w, 1000, torch.device("cpu"))
+    u0, v0, us, vs = bench.schnakenberg_initial_state(w, 1000)
     assert us == pytest.approx(0.703) and vs == pytest.approx(0.7 / (0.703 ** 2 + 0.06))
-    du = u0.numpy() / us - 1.0
-    dv = v0.numpy() / vs - 1.0
+    du = u0 / us - 1.0
+    dv = v0 / vs - 1.0
     assert np.abs(du).max() <= 0.01 and np.abs(dv).max() <= 0.01
     assert abs(du.mean()) < 2e-3 and du.std() > 4e-3  # uniform on [-1 %, 1 %]
     assert 1.0 / (w["Du"] * w["dt"]) == pytest.approx(1e5) and 1.0 / (w["Dv"] * w["dt"]) == pytest.approx(1e3)
+
+
+def test_apply_wrappers_check_their_vectors(lib):
+    """The binding's operator wrappers reject vectors that are not whole
+    right-hand sides, a mismatched output and a shift list of the wrong
+    length before anything reaches the library (checked with a fake band
+    size on CPU tensors)."""
+    from paper_2110_06322_gb300 import cpm
+    h = C.c_void_p(0x1000)
+    cpm.Band._sizes[h.value] = 10
+    try:
+        x = torch.zeros(20, dtype=torch.float64)
+        assert cpm._apply_args(h, [1.0, 2.0], x, torch.zeros(20, dtype=torch.float64))[0] == 2
+        with pytest.raises(ValueError):
+            cpm._apply_args(h, 1.0, torch.zeros(15, dtype=torch.float64), torch.zeros(15, dtype=torch.float64))
+        with pytest.raises(ValueError):
+            cpm._apply_args(h, [1.0], x, torch.zeros(20, dtype=torch.float64))
+        with pytest.raises(ValueError):
+            cpm._apply_args(h, 1.0, x, torch.zeros(20, dtype=torch.float32))
+        with pytest.raises(ValueError):
+            cpm._apply_args(h, 1.0, x, torch.zeros(10, dtype=torch.float64))
+    finally:
+        cpm.Band._sizes.pop(h.value)
+
+
+def test_tuning_arguments_are_rejected(lib):
+    from paper_2110_06322_gb300 import cpm
+    t = cpm.oras_tuning(0, 0, 0)
+    assert lib.oras_set_tuning(None, C.byref(t)) == cpm.CPM_ERR_ARG
+    assert lib.cpm_device_allocations() >= 0
