@@ -161,6 +161,14 @@ typedef struct {
                      0 by degree: 2 for p = 3 (fewer GMRES iterations and
                      shallower sweeps), 1 for p = 2 (where the shell order
                      costs iterations) */
+  int32_t coarse; /* 0 one-level (the paper's preconditioners); 1 two-level:
+                     a coarse correction on the space Z of one constant per
+                     disjoint part, E0 = Z^T M Z, applied before the
+                     one-level apply: q = Z E0^{-1} Z^T r,
+                     z = q + P_1(r - M q) (transposed: t = P_1^T r,
+                     z = t + Z E0^{-T} Z^T (r - M^T t)).  The paper names a
+                     coarse grid correction as future work (Section 4.1.1);
+                     this is the reading built here. */
 } oras_params;
 
 /* oras_setup -- partition, overlap growth, local matrices A_j = R_j M R_j^T
@@ -180,12 +188,17 @@ cpm_status oras_apply(const oras_pc* pc, const void* r, void* z, cpm_dtype dtype
                       void* stream);
 
 /* Run-time settings of a preconditioner's apply.  None changes the result of
- * a successful apply; they choose among equivalent kernels and exercise the
- * failure path.  The paper has no counterpart (its subdomain solves are PETSc
- * calls, Section 4.1.1).
+ * a successful apply beyond the summation order inside a row; they choose
+ * among equivalent kernels and exercise the failure path.  The paper has no
+ * counterpart (its subdomain solves are PETSc calls, Section 4.1.1).
  *   xplace         where each subdomain's local vector lives during the
  *                  triangular sweeps: 0 in shared memory when it fits beside the
  *                  factor ring (default), 1 always in a global-memory slice
+ *   lanes          lanes of a warp per factor row in the sweeps: 4, 8 or 16
+ *                  (0: 8 with the local vector in shared memory, 4 in a global
+ *                  slice)
+ *   schedule       order in which subdomains are handed to CTAs: 0 longest
+ *                  first (default), 1 partition order
  *   probe_timeout  0 normal; 1 failure-path test: the first factor-chunk wait
  *                  of every subdomain waits on a barrier that nothing completes,
  *                  so each CTA runs out after wait_polls polls, waits for its
@@ -197,10 +210,22 @@ cpm_status oras_apply(const oras_pc* pc, const void* r, void* z, cpm_dtype dtype
  * while no apply of pc is running. */
 typedef struct {
   int32_t xplace;
+  int32_t lanes;
+  int32_t schedule;
   int32_t probe_timeout;
   int64_t wait_polls;
 } oras_tuning;
 cpm_status oras_set_tuning(oras_pc* pc, const oras_tuning* t);
+cpm_status oras_get_tuning(const oras_pc* pc, oras_tuning* t);
+
+/* oras_autotune -- time every combination of xplace (both when the local
+ * vectors fit in shared memory), lanes (4, 8, 16) and schedule (0, 1) on
+ * `reps` forward applies of dtype (CPM_F32 or CPM_F64) each, with CUDA events
+ * on `stream`, and keep the fastest as the preconditioner's setting (the
+ * probe stays off).  best (HOST, may be NULL) receives it and best_ms (HOST,
+ * may be NULL) its time per apply.  Allocates two vectors of N_A values for
+ * the duration of the call; synchronises the stream. */
+cpm_status oras_autotune(oras_pc* pc, cpm_dtype dtype, int reps, void* stream, oras_tuning* best, double* best_ms);
 
 /* Sizes of the preconditioner: number of parts, sum of |S_j|, sum of nnz(A_j),
  * and the largest number of forward-solve levels of any subdomain.  Host pointers. */

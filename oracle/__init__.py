@@ -77,7 +77,8 @@ def lib():
         "orc_apply_rows": (None, [vp, f64, _f64p, i64, _i64p, _f64p]),
         "orc_apply_T_cols": (None, [vp, f64, _f64p, i64, _i64p, _f64p]),
         "orc_dense_solve": (i32, [i64, _f64p, _f64p, _f64p, i32]),
-        "orc_oras_setup": (vp, [vp, vp, i32, i32, i32, f64, f64, i32, i32, pi32]),
+        "orc_oras_setup": (vp, [vp, vp, i32, i32, i32, f64, f64, i32, i32, i32, pi32]),
+        "orc_oras_coarse_matrix": (None, [vp, _f64p]),
         "orc_oras_free": (None, [vp]),
         "orc_oras_partition": (None, [vp, _i32p]),
         "orc_oras_sub_size": (i64, [vp, i32]),
@@ -239,10 +240,14 @@ class ORAS:
     LOCAL_CANONICAL, LOCAL_DISTANCE, LOCAL_SHELLS = 0, 1, 2
 
     def __init__(self, band, M, nparts, overlap, robin=False, alpha=4.0, alpha_cross=20.0, exact=False,
-                 order=LOCAL_DISTANCE):
+                 order=LOCAL_DISTANCE, coarse=False):
+        """coarse=True: the two-level variant, a coarse correction on one
+        constant per disjoint part applied before the one-level apply
+        (z = q + P_RAS (r - M q), q = Z (Z^T M Z)^{-1} Z^T r)."""
         st = C.c_int()
         ptr = lib().orc_oras_setup(band._p, M._p, int(nparts), int(overlap), int(bool(robin)), float(alpha),
-                                   float(alpha_cross), int(bool(exact)), int(order), C.byref(st))
+                                   float(alpha_cross), int(bool(exact)), int(order), int(bool(coarse)),
+                                   C.byref(st))
         if not ptr:
             raise RuntimeError(f"oracle ORAS setup failed with status {st.value}")
         self._p = C.c_void_p(ptr)
@@ -275,6 +280,12 @@ class ORAS:
 
     def sub_matrix(self, j):
         return CSR(lib().orc_oras_sub_matrix_unfactored(self.band._p, self.M._p, self._p, j))
+
+    def coarse_matrix(self):
+        """E0 = Z^T M Z of the two-level variant (np x np)."""
+        E = np.zeros((self.nparts, self.nparts))
+        lib().orc_oras_coarse_matrix(self._p, E)
+        return E
 
     def apply(self, r, transpose=False):
         z = np.zeros(self.n)

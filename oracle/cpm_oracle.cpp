@@ -516,6 +516,13 @@ struct ORAS {
   int64_t n = 0;
   std::vector<int32_t> part;
   std::vector<Sub> sub;
+  // two-level variant (coarse = 1): coarse space Z with one column per
+  // disjoint part, Z_{i,a} = 1 if node i lies in part a; coarse matrix
+  // E0 = Z^T M Z (dense, LU-factored in place)
+  int coarse = 0;
+  const CSR* M = nullptr;
+  std::vector<double> E0;
+  std::vector<int32_t> E0piv;
 };
 
 int dense_lu(int64_t n, std::vector<double>& A, std::vector<int32_t>& piv) {
@@ -767,7 +774,7 @@ int oras_setup(const Band& B, const CSR& M, ORAS& P) {
 // z = sum_j Rtilde_j^T A_j^{-1} R_j r (restricted additive Schwarz, Section
 // 2.2: local solves on the overlapping S_j, recombined on the disjoint parts).
 // Transposed: z = sum_j R_j^T A_j^{-T} Rtilde_j r, summed over j ascending.
-void oras_apply(const ORAS& P, const double* r, double* z, int transpose) {
+void oras_apply_one_level(const ORAS& P, const double* r, double* z, int transpose) {
   if (!transpose) {
     for (int j = 0; j < P.np; ++j) {
       const Sub& s = P.sub[j];
@@ -788,6 +795,63 @@ void oras_apply(const ORAS& P, const double* r, double* z, int transpose) {
       else ilu_solve_T(s, x.data());
       for (size_t q = 0; q < x.size(); ++q) z[s.nodes[q]] = z[s.nodes[q]] + x[q];
     }
+  }
+}
+
+// Coarse matrix of the two-level variant: E0[a][b] = sum over nodes i of part
+// a and columns k of part b of M_ik (rows ascending, entries in CSR order).
+int coarse_setup(ORAS& P, const CSR& M) {
+  const int np = P.np;
+  P.M = &M;
+  P.E0.assign((size_t)np * np, 0.0);
+  for (int64_t i = 0; i < M.nr; ++i) {
+    const int a = P.part[i];
+    for (int64_t q = M.ptr[i]; q < M.ptr[i + 1]; ++q) {
+      double& e = P.E0[(size_t)a * np + P.part[M.col[q]]];
+      e = e + M.val[q];
+    }
+  }
+  return dense_lu(np, P.E0, P.E0piv) ? 6 : 0;
+}
+
+// y[a] = sum of v over the nodes of part a (Z^T v), nodes ascending
+void coarse_restrict(const ORAS& P, const double* v, std::vector<double>& y) {
+  y.assign(P.np, 0.0);
+  for (int64_t i = 0; i < P.n; ++i) y[P.part[i]] = y[P.part[i]] + v[i];
+}
+
+// Schwarz preconditioner, one- or two-level.  The two-level variant adds a
+// coarse correction on Z (one constant per disjoint part) multiplicatively
+// before the one-level apply:
+//     q = Z E0^{-1} Z^T r,   z = q + P_RAS (r - M q),
+// i.e. P2 = Q + P_RAS (I - M Q) with Q = Z E0^{-1} Z^T.  Its transpose is
+//     t = P_RAS^T r,   z = t + Z E0^{-T} Z^T (r - M^T t).
+void oras_apply(const ORAS& P, const double* r, double* z, int transpose) {
+  if (!P.coarse) {
+    oras_apply_one_level(P, r, z, transpose);
+    return;
+  }
+  const int64_t n = P.n;
+  const CSR& M = *P.M;
+  std::vector<double> y, t(n);
+  if (!transpose) {
+    coarse_restrict(P, r, y);
+    dense_lu_solve(P.np, P.E0, P.E0piv, y.data(), 0);
+    std::vector<double> q(n);
+    for (int64_t i = 0; i < n; ++i) q[i] = y[P.part[i]];
+    csr_matvec(M, q.data(), t.data());
+    for (int64_t i = 0; i < n; ++i) t[i] = r[i] - t[i];
+    oras_apply_one_level(P, t.data(), z, 0);
+    for (int64_t i = 0; i < n; ++i) z[i] = z[i] + q[i];
+  } else {
+    oras_apply_one_level(P, r, t.data(), 1);
+    std::vector<double> mt(n, 0.0);  // M^T t, scattered row by row
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t q = M.ptr[i]; q < M.ptr[i + 1]; ++q) mt[M.col[q]] = mt[M.col[q]] + M.val[q] * t[i];
+    for (int64_t i = 0; i < n; ++i) mt[i] = r[i] - mt[i];
+    coarse_restrict(P, mt.data(), y);
+    dense_lu_solve(P.np, P.E0, P.E0piv, y.data(), 1);
+    for (int64_t i = 0; i < n; ++i) z[i] = t[i] + y[P.part[i]];
   }
 }
 
@@ -1038,7 +1102,7 @@ int orc_dense_solve(int64_t n, const double* A, const double* rhs, double* x, in
 }
 
 void* orc_oras_setup(const void* b, const void* m, int nparts, int overlap, int robin, double alpha,
-                     double alpha_cross, int exact, int order, int* status) {
+                     double alpha_cross, int exact, int order, int coarse, int* status) {
   const Band* B = (const Band*)b;
   ORAS* P = new ORAS();
   P->np = nparts;
@@ -1055,11 +1119,28 @@ void* orc_oras_setup(const void* b, const void* m, int nparts, int overlap, int 
     return nullptr;
   }
   *status = oras_setup(*B, *(const CSR*)m, *P);
+  if (!*status && coarse) {
+    P->coarse = 1;
+    *status = coarse_setup(*P, *(const CSR*)m);
+  }
   if (*status) {
     delete P;
     return nullptr;
   }
   return P;
+}
+
+// Coarse matrix E0 = Z^T M Z of a two-level preconditioner (np x np, row-major),
+// before factorisation (assembled again).
+void orc_oras_coarse_matrix(const void* p, double* out) {
+  const ORAS* P = (const ORAS*)p;
+  const CSR& M = *P->M;
+  std::memset(out, 0, sizeof(double) * (size_t)P->np * P->np);
+  for (int64_t i = 0; i < M.nr; ++i)
+    for (int64_t q = M.ptr[i]; q < M.ptr[i + 1]; ++q) {
+      double& e = out[(size_t)P->part[i] * P->np + P->part[M.col[q]]];
+      e = e + M.val[q];
+    }
 }
 
 void orc_oras_free(void* p) { delete (ORAS*)p; }

@@ -33,11 +33,12 @@ class cpm_surface(C.Structure):
 
 class oras_params(C.Structure):
     _fields_ = [("nparts", C.c_int32), ("overlap", C.c_int32), ("robin", C.c_int32), ("alpha", C.c_double),
-                ("alpha_cross", C.c_double), ("store", C.c_int32), ("order", C.c_int32)]
+                ("alpha_cross", C.c_double), ("store", C.c_int32), ("order", C.c_int32), ("coarse", C.c_int32)]
 
 
 class oras_tuning(C.Structure):
-    _fields_ = [("xplace", C.c_int32), ("probe_timeout", C.c_int32), ("wait_polls", C.c_int64)]
+    _fields_ = [("xplace", C.c_int32), ("lanes", C.c_int32), ("schedule", C.c_int32), ("probe_timeout", C.c_int32),
+                ("wait_polls", C.c_int64)]
 
 
 class cpm_solve_params(C.Structure):
@@ -83,6 +84,8 @@ def lib():
         "oras_apply": (i32, [vp, vp, vp, i32, i32, i32, vp]),
         "oras_info": (i32, [vp, P(C.c_int32), P(C.c_int64), P(C.c_int64), P(C.c_int32)]),
         "oras_set_tuning": (i32, [vp, P(oras_tuning)]),
+        "oras_get_tuning": (i32, [vp, P(oras_tuning)]),
+        "oras_autotune": (i32, [vp, i32, i32, vp, P(oras_tuning), P(C.c_double)]),
         "cpm_device_allocations": (C.c_int64, []),
         "oras_export": (i32, [vp, vp, vp, vp, vp]),
         "cpm_solve": (i32, [vp, vp, f64, vp, vp, P(cpm_solve_params), P(cpm_solve_info), vp]),
@@ -106,7 +109,8 @@ def lib():
 
 
 EXPORTED = ["cpm_last_error", "cpm_band_build", "cpm_band_info", "cpm_band_export", "cpm_band_weights", "cpm_apply",
-            "oras_setup", "oras_apply", "oras_info", "oras_set_tuning", "oras_export", "cpm_solve",
+            "oras_setup", "oras_apply", "oras_info", "oras_set_tuning", "oras_get_tuning", "oras_autotune",
+            "oras_export", "cpm_solve",
             "cpm_solve_adjoint", "cpm_band_free", "oras_free", "cpm_kernel_launches", "cpm_device_allocations",
             "cpm_apply_noalloc", "cpm_imex_rhs", "cpm_imex_rhs_adjoint", "cpm_dot", "cpm_solve_batch"]
 
@@ -180,9 +184,28 @@ def cpm_device_allocations():
     return lib().cpm_device_allocations()
 
 
-def oras_set_tuning(pc, xplace=0, probe_timeout=0, wait_polls=0):
-    t = oras_tuning(int(xplace), int(probe_timeout), int(wait_polls))
+def oras_set_tuning(pc, xplace=0, lanes=0, schedule=0, probe_timeout=0, wait_polls=0):
+    t = oras_tuning(int(xplace), int(lanes), int(schedule), int(probe_timeout), int(wait_polls))
     _check(lib().oras_set_tuning(pc, C.byref(t)))
+
+
+def _tuning_dict(t):
+    return {"xplace": t.xplace, "lanes": t.lanes, "schedule": t.schedule, "probe_timeout": t.probe_timeout,
+            "wait_polls": t.wait_polls}
+
+
+def oras_get_tuning(pc):
+    t = oras_tuning()
+    _check(lib().oras_get_tuning(pc, C.byref(t)))
+    return _tuning_dict(t)
+
+
+def oras_autotune(pc, dtype=CPM_F32, reps=3, stream=None):
+    """Time the equivalent apply kernels and keep the fastest; returns
+    (setting, milliseconds per apply)."""
+    t, ms = oras_tuning(), C.c_double()
+    _check(lib().oras_autotune(pc, int(dtype), int(reps), _stream(stream), C.byref(t), C.byref(ms)))
+    return _tuning_dict(t), ms.value
 
 
 def _rx(prm):
@@ -209,9 +232,9 @@ def cpm_dot(band, a, b, out, stream=None):
 
 
 def oras_setup(band, c, nparts, overlap, robin=False, alpha=4.0, alpha_cross=20.0, store=CPM_F32, order=0,
-               stream=None):
+               coarse=False, stream=None):
     prm = oras_params(int(nparts), int(overlap), int(bool(robin)), float(alpha), float(alpha_cross), int(store),
-                      int(order))
+                      int(order), int(bool(coarse)))
     out = C.c_void_p()
     _check(lib().oras_setup(band, C.byref(prm), float(c), _stream(stream), C.byref(out)))
     return out
@@ -326,10 +349,12 @@ class Schwarz:
     """(O)RAS preconditioner over a Band (Section 2.2)."""
 
     def __init__(self, band, c, nparts, overlap, robin=False, alpha=4.0, alpha_cross=20.0, store=CPM_F32, order=0,
-                 stream=None):
+                 coarse=False, stream=None):
         self.band = band
         self.c = float(c)
-        self.handle = oras_setup(band.handle, c, nparts, overlap, robin, alpha, alpha_cross, store, order, stream)
+        self.coarse = bool(coarse)
+        self.handle = oras_setup(band.handle, c, nparts, overlap, robin, alpha, alpha_cross, store, order, coarse,
+                                 stream)
         npt, rows, nnz, lev = C.c_int32(), C.c_int64(), C.c_int64(), C.c_int32()
         _check(lib().oras_info(self.handle, C.byref(npt), C.byref(rows), C.byref(nnz), C.byref(lev)))
         self.nparts, self.total_rows, self.total_nnz, self.max_levels = npt.value, rows.value, nnz.value, lev.value
@@ -344,10 +369,17 @@ class Schwarz:
         z = torch.empty_like(r) if out is None else out
         return oras_apply(self.handle, r, z, self.band.n_active, transpose, stream)
 
-    def set_tuning(self, xplace=0, probe_timeout=0, wait_polls=0):
+    def set_tuning(self, xplace=0, lanes=0, schedule=0, probe_timeout=0, wait_polls=0):
         """Run-time settings of the apply (oras_set_tuning): local-vector
-        placement, the failure-path probe and the wait bound."""
-        oras_set_tuning(self.handle, xplace, probe_timeout, wait_polls)
+        placement, lanes per factor row, subdomain schedule, the
+        failure-path probe and the wait bound."""
+        oras_set_tuning(self.handle, xplace, lanes, schedule, probe_timeout, wait_polls)
+
+    def tuning(self):
+        return oras_get_tuning(self.handle)
+
+    def autotune(self, dtype=CPM_F32, reps=3, stream=None):
+        return oras_autotune(self.handle, dtype, reps, stream)
 
     def export(self, stream=None):
         d = self.band.device

@@ -135,10 +135,14 @@ __global__ void __launch_bounds__(256) k_erow_apply(ApplyGeom G, const T* __rest
 constexpr int EGROUP_MAX = 16;
 constexpr int EGROUP_WIN = 256;  // items are ordered by row count within windows of this many
 
+// Each row of an item is one aligned 16-byte record {s_x, s_y, s_z, row}
+// (offsets in the cube, row index as bits); the next row's record is loaded
+// while the current row is evaluated, so the DRAM latency of the record
+// stream overlaps the arithmetic instead of stalling every row.
 template <int P>
 __global__ void __launch_bounds__(EGROUP_WIN)
-    k_erow_grp(ApplyGeom G, int64_t nitem, const int2* __restrict__ items, const int32_t* __restrict__ grow,
-               const float* __restrict__ gs, const float* __restrict__ x, float* __restrict__ w) {
+    k_erow_grp(ApplyGeom G, int64_t nitem, const int2* __restrict__ items, const float4* __restrict__ grec,
+               const float* __restrict__ x, float* __restrict__ w) {
   const int rhs = blockIdx.y;
   x += (int64_t)rhs * G.nA;
   w += (int64_t)rhs * G.nR * 2;
@@ -163,12 +167,15 @@ __global__ void __launch_bounds__(EGROUP_WIN)
       for (int v = 0; v <= P; ++v)
 #pragma unroll
         for (int t = 0; t <= P; ++t) X[u][v][t] -= xref;
+    float4 nxt = __ldg(grec + start);
     for (int k = 0; k < rows; ++k) {
-      const int pos = start + k;
-      const int32_t r = grow[pos];
+      const float4 cur = nxt;
+      if (k + 1 < rows) nxt = __ldg(grec + start + k + 1);
+      const int32_t r = __float_as_int(cur.w);
       float l[3][P + 1];
-#pragma unroll
-      for (int d = 0; d < 3; ++d) lagrange_f32<P>(gs[3 * pos + d], l[d]);
+      lagrange_f32<P>(cur.x, l[0]);
+      lagrange_f32<P>(cur.y, l[1]);
+      lagrange_f32<P>(cur.z, l[2]);
       float acc = 0;
 #pragma unroll
       for (int u = 0; u <= P; ++u) {
@@ -252,11 +259,10 @@ __global__ void __launch_bounds__(EGROUP_WIN) k_gwin(int64_t nitem, const int2* 
     out[w0 + pos] = sh[t];
   }
 }
-__global__ void k_gs32(int64_t nR, const int32_t* __restrict__ grow, const float* __restrict__ s32, float* gs) {
+__global__ void k_grec(int64_t nR, const int32_t* __restrict__ grow, const float* __restrict__ s32, float4* rec) {
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nR; p += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = grow[p];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) gs[3 * p + d] = s32[3 * r + d];
+    const int32_t r = grow[p];
+    rec[p] = make_float4(s32[3 * (int64_t)r], s32[3 * (int64_t)r + 1], s32[3 * (int64_t)r + 2], __int_as_float(r));
   }
 }
 
@@ -457,8 +463,9 @@ cpm_status erow_pass(const cpm_band* B, const ApplyGeom& G, const T* x, T* w, in
   if constexpr (sizeof(T) == 4) {
     dim3 g1(grid_for(B->nitem, EGROUP_WIN), nr);
     const int2* it = reinterpret_cast<const int2*>(B->gitem);
-    if (B->p == 3) KL(k_erow_grp<3><<<g1, EGROUP_WIN, 0, s>>>(G, B->nitem, it, B->grow, B->gs32, x, w));
-    else KL(k_erow_grp<2><<<g1, EGROUP_WIN, 0, s>>>(G, B->nitem, it, B->grow, B->gs32, x, w));
+    const float4* rec = reinterpret_cast<const float4*>(B->grec);
+    if (B->p == 3) KL(k_erow_grp<3><<<g1, EGROUP_WIN, 0, s>>>(G, B->nitem, it, rec, x, w));
+    else KL(k_erow_grp<2><<<g1, EGROUP_WIN, 0, s>>>(G, B->nitem, it, rec, x, w));
   } else {
     dim3 g1(grid_for(B->nR, 256), nr);
     if (B->p == 3) KL(k_erow_apply<T, 3><<<g1, 256, 0, s>>>(G, x, w));
@@ -549,7 +556,7 @@ cpm_status build_erow_groups(cpm_band* B, cudaStream_t s) {
   if ((st = dalloc(&kptr, nA + 1, s)) != CPM_OK) return done(st);
   if ((st = dalloc(&iptr, nA + 1, s)) != CPM_OK) return done(st);
   if ((st = dalloc(&B->grow, nR, s)) != CPM_OK) return done(st);
-  if ((st = dalloc(&B->gs32, 3 * nR, s)) != CPM_OK) return done(st);
+  if ((st = dalloc(&B->grec, 4 * nR, s)) != CPM_OK) return done(st);
   CPM_CUDA(cudaMemsetAsync(cnt, 0, nA * sizeof(int32_t), s));
   KL(k_gkey<<<grid_for(nR, 256), 256, 0, s>>>(G, key, cnt));
   if ((st = scan_exclusive_i32(cnt, kptr, nA, s)) != CPM_OK) return done(st);
@@ -564,7 +571,8 @@ cpm_status build_erow_groups(cpm_band* B, cudaStream_t s) {
   KL(k_gitems<<<grid_for(nA, 256), 256, 0, s>>>(nA, kptr, iptr, tmp));
   const int64_t nwin = (B->nitem + EGROUP_WIN - 1) / EGROUP_WIN;
   KL(k_gwin<<<(unsigned)nwin, EGROUP_WIN, 0, s>>>(B->nitem, tmp, reinterpret_cast<int2*>(B->gitem)));
-  KL(k_gs32<<<grid_for(nR, 256), 256, 0, s>>>(nR, B->grow, B->s32, B->gs32));
+  KL(k_grec<<<grid_for(nR, 256), 256, 0, s>>>(nR, B->grow, B->s32, reinterpret_cast<float4*>(B->grec)));
+  dfree(B->grow, s);  // the records carry the row indices
   CPM_CUDA(cudaGetLastError());
   return done(CPM_OK);
 }

@@ -379,7 +379,7 @@ void band_free(cpm_band* B, cudaStream_t s) {
   dfree(B->tw32, s);
   dfree(B->gitem, s);
   dfree(B->grow, s);
-  dfree(B->gs32, s);
+  dfree(B->grec, s);
   if (B->wbuf) cudaFreeAsync(B->wbuf, s);
   B->wbuf = nullptr;
   delete B;

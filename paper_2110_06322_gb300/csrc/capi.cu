@@ -120,6 +120,7 @@ cpm_status oras_setup(const cpm_band* band, const oras_params* prm, double c, vo
     return fail(CPM_ERR_ARG, "store must be CPM_F64, CPM_F32 or CPM_BF16");
   if (prm->order < 0 || prm->order > 2)
     return fail(CPM_ERR_ARG, "order must be 0 (by degree), 1 (distance) or 2 (shells)");
+  if (prm->coarse != 0 && prm->coarse != 1) return fail(CPM_ERR_ARG, "coarse must be 0 or 1");
   if (!std::isfinite(c)) return fail(CPM_ERR_NAN, "shift c is not finite");
   g_err[0] = 0;
   oras_params q = *prm;
@@ -140,12 +141,30 @@ cpm_status oras_apply(const oras_pc* pc, const void* r, void* z, cpm_dtype dtype
 cpm_status oras_set_tuning(oras_pc* pc, const oras_tuning* t) {
   if (!pc || !t) return fail(CPM_ERR_ARG, "null argument");
   if (t->xplace != 0 && t->xplace != 1) return fail(CPM_ERR_ARG, "xplace must be 0 or 1");
+  if (t->lanes != 0 && t->lanes != 4 && t->lanes != 8 && t->lanes != 16)
+    return fail(CPM_ERR_ARG, "lanes must be 0, 4, 8 or 16");
+  if (t->schedule != 0 && t->schedule != 1) return fail(CPM_ERR_ARG, "schedule must be 0 or 1");
   if (t->probe_timeout != 0 && t->probe_timeout != 1) return fail(CPM_ERR_ARG, "probe_timeout must be 0 or 1");
   if (t->wait_polls < 0 || t->wait_polls > 0xffffffffll) return fail(CPM_ERR_ARG, "wait_polls must be in [0, 2^32)");
   pc->xplace = t->xplace;
+  pc->lanes = t->lanes;
+  pc->schedule = t->schedule;
   pc->probe_timeout = t->probe_timeout;
   pc->wait_polls = t->wait_polls;
   return CPM_OK;
+}
+
+cpm_status oras_get_tuning(const oras_pc* pc, oras_tuning* t) {
+  if (!pc || !t) return fail(CPM_ERR_ARG, "null argument");
+  *t = oras_tuning{pc->xplace, pc->lanes, pc->schedule, pc->probe_timeout, pc->wait_polls};
+  return CPM_OK;
+}
+
+cpm_status oras_autotune(oras_pc* pc, cpm_dtype dtype, int reps, void* stream, oras_tuning* best, double* best_ms) {
+  if (!pc) return fail(CPM_ERR_ARG, "null preconditioner");
+  if (dtype != CPM_F32 && dtype != CPM_F64) return fail(CPM_ERR_ARG, "dtype must be CPM_F32 or CPM_F64");
+  if (reps < 1 || reps > 1000) return fail(CPM_ERR_ARG, "reps must be in [1, 1000]");
+  return oras_tune(pc, dtype, reps, as_stream(stream), best, best_ms);
 }
 
 cpm_status oras_info(const oras_pc* pc, int32_t* nparts, int64_t* total_rows, int64_t* total_nnz,

@@ -145,8 +145,9 @@ struct cpm_band {
   // base are consecutive in grow; a work item is at most EGROUP_MAX of them
   int64_t nitem = 0;
   int32_t* gitem = nullptr;      // [nitem][2] {first position << 4 | (rows - 1), base node (canonical rank)}
-  int32_t* grow = nullptr;       // [nR] E rows in cube-base order (ascending row within a cube)
-  float* gs32 = nullptr;         // [nR][3] FP32 offsets of those rows, same order
+  int32_t* grow = nullptr;       // [nR] E rows in cube-base order (set-up only)
+  float* grec = nullptr;         // [nR][4] per row in that order: FP32 offsets s_x, s_y, s_z and the row
+                                 // index (as the bits of the fourth float), one 16-byte record
   // scratch for the operator apply
   void* wbuf = nullptr;          // [nR] E x values (FP64 room)
   size_t wbuf_bytes = 0;

@@ -922,6 +922,7 @@ cpm_status oras_build(const cpm_band* B, const oras_params* prm, double c, cudaS
   P->overlap = prm->overlap;
   P->robin = prm->robin;
   P->order = prm->order;
+  P->coarse = prm->coarse;
   P->alpha = prm->alpha;
   P->alpha_x = prm->alpha_cross;
   P->store = prm->store;
@@ -1068,6 +1069,7 @@ cpm_status oras_build(const cpm_band* B, const oras_params* prm, double c, cudaS
     TRYC(cudaMemsetAsync(P->dpos, 0xff, nloc * sizeof(int32_t), s));
     KL(k_local<<<G, LOC_WARPS * 32, 0, s>>>(A, P->rptr, nullptr, P->col, P->val, P->dpos, err));
     TRYC(cudaGetLastError());
+    if (P->coarse) TRY(coarse_build(P, mptr, mcol, mval, s));
     dfree(mptr, s);
     dfree(mcol, s);
     dfree(mval, s);
@@ -1139,6 +1141,7 @@ void oras_destroy(oras_pc* P, cudaStream_t s) {
   dfree(P->mloc, s);
   dfree(P->lsub, s);
   for (auto& pf : P->packed) packed_free(pf, s);
+  coarse_free(P, s);
   dfree(P->err, s);
   delete P;
 }

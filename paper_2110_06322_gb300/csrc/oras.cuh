@@ -75,8 +75,17 @@ struct oras_pc {
   int* err = nullptr;         // device flag: a bounded wait of the apply ran out
   // run-time settings of the apply (oras_set_tuning)
   int xplace = 0;             // 0 local vector in shared memory when it fits, 1 always a global slice
+  int lanes = 0;              // lanes per factor row in the sweeps (0: by placement)
+  int schedule = 0;           // 0 subdomains longest first, 1 in partition order
   int probe_timeout = 0;      // failure-path test: the first chunk wait can only run out
   int64_t wait_polls = 0;     // polls of each consumer-side wait (0: the default)
+  // two-level variant (coarse correction on one constant per disjoint part)
+  int coarse = 0;
+  int64_t* mzptr = nullptr;   // [nA+1] rows of M Z: the parts each node's row reaches
+  int32_t* mzpart = nullptr;  // [nmz] part
+  double* mzval = nullptr;    // [nmz] the row's sum over that part (FP64)
+  float* mzval32 = nullptr;   // [nmz] the same in FP32
+  double* E0inv = nullptr;    // [np][np] inverse of Z^T M Z, row-major
 };
 
 namespace cpm {
@@ -86,6 +95,13 @@ constexpr int KMEM = 16;  // most subdomains one node may belong to
 namespace cpm {
 cpm_status oras_build(const cpm_band* B, const oras_params* prm, double c, cudaStream_t s, oras_pc** out);
 cpm_status oras_run(const oras_pc* P, const void* r, void* z, cpm_dtype dt, int nrhs, int transpose, cudaStream_t s);
+cpm_status oras_run_one_level(const oras_pc* P, const void* r, void* z, cpm_dtype dt, int nrhs, int transpose,
+                              cudaStream_t s);
+// coarse.cu: the two-level variant
+cpm_status coarse_build(oras_pc* P, const int64_t* mptr, const int32_t* mcol, const double* mval, cudaStream_t s);
+void coarse_free(oras_pc* P, cudaStream_t s);
+cpm_status coarse_apply(const oras_pc* P, const void* r, void* z, cpm_dtype dt, int nrhs, int transpose,
+                        cudaStream_t s);
 cpm_status pack_factors(oras_pc* P, int transposed, const cpm_dtype* vt, PackedFactors* out, int nout,
                         cudaStream_t s);
 void packed_free(PackedFactors& pf, cudaStream_t s);
@@ -93,6 +109,8 @@ void oras_destroy(oras_pc* P, cudaStream_t s);
 // Read and clear the preconditioner's timeout flag (synchronises the stream):
 // CPM_ERR_TIMEOUT if a bounded wait of an apply since the last check ran out.
 cpm_status oras_take_error(const oras_pc* P, cudaStream_t s);
+// time the equivalent apply kernels and keep the fastest (oras_autotune)
+cpm_status oras_tune(oras_pc* P, cpm_dtype dt, int reps, cudaStream_t s, oras_tuning* best, double* best_ms);
 cpm_status solve_run(const cpm_band* B, const oras_pc* P, double c, const double* f, double* u,
                      const cpm_solve_params* prm, cpm_solve_info* info, int transpose, cudaStream_t s);
 }  // namespace cpm

@@ -410,6 +410,7 @@ struct PkArgs {
   int* err;
   uint32_t wait_limit;  // polls of each consumer-side wait before it gives up
   int probe;            // failure-path test: the first chunk wait waits on a barrier nothing completes
+  int natural;          // subdomains in partition order instead of longest first
 };
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -432,33 +433,37 @@ __device__ __forceinline__ bool consumer_sync_or(bool v) {
 }
 
 // partial dot product of one packed row with the local vector: lane `sub`
-// of the row's LPR lanes takes entries e0 + sub, e0 + sub + LPR, ...
-template <typename T, typename V, int LPR>
+// of the row's LPR lanes takes entries e0 + sub, e0 + sub + LPR, ...  UNR
+// entries are loaded before they are used, so UNR gathers of the local
+// vector are in flight at once: a few for a local vector in shared memory
+// (short latency), enough to cover a whole row when it lives in a global
+// slice (one L2 round trip per row instead of several).
+template <typename T, typename V, int LPR, int UNR>
 __device__ __forceinline__ T row_dot(const int4 h, int e0, int sub, const V* vals, const uint16_t* cols,
                                      const T* xs) {
   T s = 0;
-#pragma unroll 4
+#pragma unroll UNR
   for (int e = e0 + sub; e < h.z; e += LPR) s += cvt<V, T>(vals[h.y + e]) * xs[cols[h.y + e]];
   return s;
 }
 
-// lanes per factor row in the Schwarz sweeps: 32 / LPR rows share each
-// shuffle of the row reductions.  Rows hold ~60 entries; 8 lanes per row
-// measured best for FP32 and FP64 on the 512-part torus (16 and 32 lanes
-// spend more issue slots and FP64 adds on the reductions).
-constexpr int SW_LPR = 8;
+// lanes per factor row in the Schwarz sweeps (a run-time choice among 4, 8
+// and 16): 32 / LPR rows share each shuffle of the row reductions.  Lower
+// and upper rows hold ~60 entries each.
+constexpr int SW_LPR_SMEM = 8;    // local vector in shared memory: measured best on the 512-part torus
+constexpr int SW_LPR_GLOBAL = 8;  // global slice: 8 also measured best (4 lanes: 1.3x slower at h = 0.002)
 
 // Warps 0..PK_WARPS-1 consume chunks; warp PK_WARPS produces them (one lane
 // issues the bulk copies).  full[s]: a chunk landed in stage s (transaction
 // count); empty[s]: the consumers finished with stage s.
-template <typename T, typename V, bool SMEMX>
+template <typename T, typename V, bool SMEMX, int SW_LPR>
 __global__ void __launch_bounds__((PK_WARPS + 1) * 32, 2)
     k_schwarz_pk(PkArgs A, const T* __restrict__ r, T* __restrict__ z, T* xglob) {
   extern __shared__ __align__(128) unsigned char pk_smem[];
   __shared__ uint64_t full[NSTAGE], empty[NSTAGE], probe_bar;
   __shared__ int abort_flag;
   int64_t issued = 0;  // chunks the producer lane has issued (used by its drain)
-  const int j = A.order[blockIdx.x], rhs = blockIdx.y;
+  const int j = A.natural ? (int)blockIdx.x : A.order[blockIdx.x], rhs = blockIdx.y;
   const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
   const bool producer = wid == PK_WARPS;
   r += (int64_t)rhs * A.nA;
@@ -543,7 +548,7 @@ __global__ void __launch_bounds__((PK_WARPS + 1) * 32, 2)
           T sdot = 0;
           if (has) {
             h = hdr[rr];
-            sdot = row_dot<T, V, LPR>(h, e0, sub, vals, cols, xs);
+            sdot = row_dot<T, V, LPR, (SMEMX ? 4 : 64 / LPR)>(h, e0, sub, vals, cols, xs);
           }
 #pragma unroll
           for (int o = LPR / 2; o > 0; o >>= 1) sdot += __shfl_xor_sync(0xffffffffu, sdot, o);
@@ -664,12 +669,21 @@ static cpm_status allow_pk_smem(cudaStream_t) {
   CPM_CUDA(cudaGetDevice(&dev));
   const unsigned long long bit = 1ull << (dev & 63);
   if (done.load() & bit) return CPM_OK;
-  CPM_CUDA(cudaFuncSetAttribute(k_schwarz_pk<T, V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)PK_SMEM_MAX));
-  CPM_CUDA(cudaFuncSetAttribute(k_schwarz_pk<T, V, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)PK_SMEM_MAX));
+  const void* fns[6] = {(const void*)k_schwarz_pk<T, V, true, 4>,  (const void*)k_schwarz_pk<T, V, true, 8>,
+                        (const void*)k_schwarz_pk<T, V, true, 16>, (const void*)k_schwarz_pk<T, V, false, 4>,
+                        (const void*)k_schwarz_pk<T, V, false, 8>, (const void*)k_schwarz_pk<T, V, false, 16>};
+  for (const void* f : fns)
+    CPM_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PK_SMEM_MAX));
   done.fetch_or(bit);
   return CPM_OK;
+}
+
+template <typename T, typename V, bool SMEMX>
+static void launch_pk(int lanes, dim3 g, size_t sm, cudaStream_t s, const PkArgs& A, const T* r, T* z, T* xl) {
+  constexpr int NT = (PK_WARPS + 1) * 32;
+  if (lanes == 4) KL(k_schwarz_pk<T, V, SMEMX, 4><<<g, NT, sm, s>>>(A, r, z, xl));
+  else if (lanes == 16) KL(k_schwarz_pk<T, V, SMEMX, 16><<<g, NT, sm, s>>>(A, r, z, xl));
+  else KL(k_schwarz_pk<T, V, SMEMX, 8><<<g, NT, sm, s>>>(A, r, z, xl));
 }
 
 template <typename T, typename V>
@@ -691,6 +705,7 @@ static cpm_status run_pk(const oras_pc* P, const PackedFactors& pf, const T* r, 
   A.csz_bytes = pad16(2 * pf.max_chunks);
   A.wait_limit = P->wait_polls > 0 ? (uint32_t)std::min<int64_t>(P->wait_polls, 0xffffffffll) : WAIT_LIMIT;
   A.probe = P->probe_timeout;
+  A.natural = P->schedule == 1;
   const size_t ring = (size_t)NSTAGE * CHUNK_BYTES + A.csz_bytes;
   const size_t xsb = (size_t)P->max_rows * sizeof(T);
   // local vector in shared memory when it fits beside the ring with two CTAs
@@ -705,12 +720,9 @@ static cpm_status run_pk(const oras_pc* P, const PackedFactors& pf, const T* r, 
     const int nr = nrhs - r0 < 65535 ? nrhs - r0 : 65535;
     dim3 g(P->np, nr);
     T* xl = xloc ? xloc + (int64_t)r0 * P->nloc : nullptr;
-    if (smemx)
-      KL(k_schwarz_pk<T, V, true><<<g, (PK_WARPS + 1) * 32, sm, s>>>(A, r + (int64_t)r0 * P->nA,
-                                                                   z + (int64_t)r0 * P->nA, xl));
-    else
-      KL(k_schwarz_pk<T, V, false><<<g, (PK_WARPS + 1) * 32, sm, s>>>(A, r + (int64_t)r0 * P->nA,
-                                                                    z + (int64_t)r0 * P->nA, xl));
+    const int lanes = P->lanes ? P->lanes : (smemx ? SW_LPR_SMEM : SW_LPR_GLOBAL);
+    if (smemx) launch_pk<T, V, true>(lanes, g, sm, s, A, r + (int64_t)r0 * P->nA, z + (int64_t)r0 * P->nA, xl);
+    else launch_pk<T, V, false>(lanes, g, sm, s, A, r + (int64_t)r0 * P->nA, z + (int64_t)r0 * P->nA, xl);
     if (transpose) {
       dim3 g2(grid_for(P->nA, 256), nr);
       KL(k_gather_T2<T><<<g2, 256, 0, s>>>(P->nA, P->nloc, P->mcnt, P->mloc, xl, z + (int64_t)r0 * P->nA));
@@ -720,6 +732,67 @@ static cpm_status run_pk(const oras_pc* P, const PackedFactors& pf, const T* r, 
   dfree(xloc, s);
   if (e != cudaSuccess) return cuda_fail(e, "packed Schwarz kernels", __FILE__, __LINE__);
   return CPM_OK;
+}
+
+// Autotuner of the apply: every (placement, lanes, schedule) combination
+// that the preconditioner allows, timed on reps forward applies of a zero
+// vector (the sweeps' work does not depend on the values), fastest kept.
+cpm_status oras_tune(oras_pc* P, cpm_dtype dt, int reps, cudaStream_t s, oras_tuning* best, double* best_ms) {
+  if (dt == CPM_F32 && P->store == CPM_F64)
+    return fail(CPM_ERR_ARG, "FP32 applies need factors stored as CPM_F32 or CPM_BF16");
+  const size_t esz = dt == CPM_F64 ? 8 : 4;
+  const int saved_probe = P->probe_timeout;
+  P->probe_timeout = 0;
+  void *r = nullptr, *z = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto done = [&](cpm_status st) {
+    dfree(r, s);
+    dfree(z, s);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    P->probe_timeout = saved_probe;
+    return st;
+  };
+  cpm_status st;
+  if ((st = dalloc((uint8_t**)&r, P->nA * esz, s)) != CPM_OK) return done(st);
+  if ((st = dalloc((uint8_t**)&z, P->nA * esz, s)) != CPM_OK) return done(st);
+  if (cudaMemsetAsync(r, 0, P->nA * esz, s) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess)
+    return done(fail(CPM_ERR_CUDA, "autotune set-up failed"));
+  oras_tuning keep{P->xplace, P->lanes, P->schedule, 0, P->wait_polls}, win = keep;
+  double win_ms = 1e300;
+  const int lanes[3] = {4, 8, 16};
+  for (int xp = 0; xp < 2; ++xp)
+    for (int li = 0; li < 3; ++li)
+      for (int sc = 0; sc < 2; ++sc) {
+        P->xplace = xp;
+        P->lanes = lanes[li];
+        P->schedule = sc;
+        if ((st = oras_run(P, r, z, dt, 1, 0, s)) != CPM_OK) return done(st);  // warm-up (packs on first use)
+        cudaEventRecord(e0, s);
+        for (int q = 0; q < reps; ++q)
+          if ((st = oras_run(P, r, z, dt, 1, 0, s)) != CPM_OK) return done(st);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) return done(fail(CPM_ERR_CUDA, "autotune timing failed"));
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms / reps < win_ms) {
+          win_ms = ms / reps;
+          win = oras_tuning{xp, lanes[li], sc, 0, keep.wait_polls};
+        }
+      }
+  if ((st = oras_take_error(P, s)) != CPM_OK) {
+    P->xplace = keep.xplace;
+    P->lanes = keep.lanes;
+    P->schedule = keep.schedule;
+    return done(st);
+  }
+  P->xplace = win.xplace;
+  P->lanes = win.lanes;
+  P->schedule = win.schedule;
+  if (best) *best = win;
+  if (best_ms) *best_ms = win_ms;
+  return done(CPM_OK);
 }
 
 cpm_status oras_take_error(const oras_pc* P, cudaStream_t s) {
@@ -733,7 +806,15 @@ cpm_status oras_take_error(const oras_pc* P, cudaStream_t s) {
   return fail(CPM_ERR_TIMEOUT, "a bounded wait in the Schwarz apply ran out");
 }
 
-cpm_status oras_run(const oras_pc* Pc, const void* r, void* z, cpm_dtype dt, int nrhs, int transpose, cudaStream_t s) {
+cpm_status oras_run(const oras_pc* P, const void* r, void* z, cpm_dtype dt, int nrhs, int transpose, cudaStream_t s) {
+  if (dt == CPM_F32 && !transpose && P->store == CPM_F64)
+    return fail(CPM_ERR_ARG, "FP32 apply needs factors stored as CPM_F32 or CPM_BF16");
+  if (P->coarse) return coarse_apply(P, r, z, dt, nrhs, transpose, s);
+  return oras_run_one_level(P, r, z, dt, nrhs, transpose, s);
+}
+
+cpm_status oras_run_one_level(const oras_pc* Pc, const void* r, void* z, cpm_dtype dt, int nrhs, int transpose,
+                              cudaStream_t s) {
   oras_pc* P = const_cast<oras_pc*>(Pc);
   if (dt == CPM_F32 && !transpose && P->store == CPM_F64)
     return fail(CPM_ERR_ARG, "FP32 apply needs factors stored as CPM_F32 or CPM_BF16");

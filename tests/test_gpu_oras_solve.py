@@ -262,6 +262,36 @@ def test_schwarz_global_slice_branch_matches_oracle(cpm, oracle_mod, torus005, r
         assert _rel(P.apply(_cuda(r)).cpu().numpy(), want) <= 1e-12
 
 
+@pytest.mark.parametrize("lanes", [4, 8, 16])
+@pytest.mark.parametrize("xplace", [0, 1])
+def test_schwarz_kernel_variants_match_oracle(cpm, oracle_mod, torus005, lanes, xplace):
+    """Every lanes-per-row variant, in both local-vector placements and both
+    subdomain schedules, against the oracle (FP64 1e-12, FP32 1e-4, forward
+    and transposed)."""
+    B, O, M = torus005
+    OP = oracle_mod.ORAS(O, M, 16, 2, order=oracle_mod.ORAS.LOCAL_SHELLS)
+    r = inputs.gaussian_vector(18, B.n_active)
+    want, wantT = OP.apply(r), OP.apply(r, transpose=True)
+    P = cpm.Schwarz(B, 10.0, 16, 2, store=cpm.CPM_F32)
+    for schedule in (0, 1):
+        P.set_tuning(xplace=xplace, lanes=lanes, schedule=schedule)
+        assert P.tuning()["lanes"] == lanes
+        assert _rel(P.apply(_cuda(r)).cpu().numpy(), want) <= 1e-12
+        assert _rel(P.apply(_cuda(r), transpose=True).cpu().numpy(), wantT) <= 1e-12
+        assert _rel(P.apply(_cuda(r).float()).double().cpu().numpy(), want) <= 1e-4
+
+
+def test_schwarz_autotune_keeps_a_valid_setting(cpm, oracle_mod, torus005):
+    B, O, M = torus005
+    P = cpm.Schwarz(B, 10.0, 16, 2, store=cpm.CPM_F32)
+    best, ms = P.autotune(cpm.CPM_F32, reps=2)
+    assert ms > 0 and best["lanes"] in (4, 8, 16) and best["schedule"] in (0, 1) and best["probe_timeout"] == 0
+    assert P.tuning() == best
+    OP = oracle_mod.ORAS(O, M, 16, 2, order=oracle_mod.ORAS.LOCAL_SHELLS)
+    r = inputs.gaussian_vector(19, B.n_active)
+    assert _rel(P.apply(_cuda(r).float()).double().cpu().numpy(), OP.apply(r)) <= 1e-4
+
+
 def test_schwarz_large_subdomains_multichunk_levels(cpm, oracle_mod, torus0025):
     """~38k-row subdomains (global-slice branch chosen by size, levels of
     several chunks): element-wise against the oracle in FP64 and FP32,
@@ -368,3 +398,56 @@ def test_p2_solves_match_direct_solve(cpm, oracle_mod, torus005_p2):
     assert info["status"] == 0, info
     ld = lu.solve(f, trans="T")
     assert np.linalg.norm(lam.cpu().numpy() - ld) <= 1e-10 * np.linalg.norm(ld)
+
+
+# ------------------------------------------------------------------ two-level (coarse correction)
+@pytest.mark.parametrize("robin", [False, True])
+def test_two_level_apply_matches_oracle(cpm, oracle_mod, torus005, robin):
+    """Coarse correction on one constant per disjoint part, then the
+    one-level apply (the oracle's two-level variant): FP64 forward and
+    transposed to 1e-12, FP32 forward to 1e-4, two right-hand sides."""
+    B, O, M = torus005
+    P = cpm.Schwarz(B, 10.0, 16, 2, robin=robin, coarse=True)
+    OP = oracle_mod.ORAS(O, M, 16, 2, robin=robin, order=oracle_mod.ORAS.LOCAL_SHELLS, coarse=True)
+    R = np.stack([inputs.gaussian_vector(80 + q, B.n_active) for q in range(2)])
+    Z = P.apply(_cuda(R).reshape(-1)).cpu().numpy().reshape(2, -1)
+    ZT = P.apply(_cuda(R).reshape(-1), transpose=True).cpu().numpy().reshape(2, -1)
+    Z32 = P.apply(_cuda(R).reshape(-1).float()).double().cpu().numpy().reshape(2, -1)
+    for q in range(2):
+        want = OP.apply(R[q])
+        assert _rel(Z[q], want) <= 1e-12
+        assert _rel(Z32[q], want) <= 1e-4
+        assert _rel(ZT[q], OP.apply(R[q], transpose=True)) <= 1e-12
+
+
+def test_two_level_solves_match_direct_solve_in_fewer_iterations(cpm, oracle_mod, torus005, torus005_lu):
+    B, O, M = torus005
+    f = inputs.gaussian_vector(85, B.n_active)
+    xd = torus005_lu.solve(f)
+    iters = {}
+    for coarse in (False, True):
+        P = cpm.Schwarz(B, 10.0, 32, 2, coarse=coarse)
+        u, info = cpm.solve(B, _cuda(f), P, rtol=1e-13, maxit=5000)
+        assert info["status"] == 0, info
+        assert np.linalg.norm(u.cpu().numpy() - xd) <= 1e-10 * np.linalg.norm(xd)
+        iters[coarse] = info["iters"]
+        u, info = cpm.solve(B, _cuda(f), P, rtol=1e-10, maxit=5000, mixed=True)
+        assert info["status"] == 0, info
+        assert np.linalg.norm(u.cpu().numpy() - xd) <= 1e-8 * np.linalg.norm(xd)
+        lam, info = cpm.solve(B, _cuda(f), P, rtol=1e-13, maxit=5000, adjoint=True)
+        assert info["status"] == 0, info
+        ld = torus005_lu.solve(f, trans="T")
+        assert np.linalg.norm(lam.cpu().numpy() - ld) <= 1e-10 * np.linalg.norm(ld)
+    assert iters[True] < iters[False], iters
+
+
+def test_two_level_with_empty_parts(cpm, oracle_mod, sphere01):
+    """More parts than the band can fill: empty parts get a decoupled unit
+    row in Z^T M Z and the solve is unaffected."""
+    B, O, M = sphere01
+    f = inputs.gaussian_vector(86, B.n_active)
+    xd = sla.spsolve(M.to_scipy().tocsc(), f)
+    P = cpm.Schwarz(B, 1.0, 1000, 1, coarse=True)
+    u, info = cpm.solve(B, _cuda(f), P, rtol=1e-12, maxit=5000)
+    assert info["status"] == 0, info
+    assert np.linalg.norm(u.cpu().numpy() - xd) <= 1e-10 * np.linalg.norm(xd)

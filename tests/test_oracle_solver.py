@@ -274,3 +274,78 @@ def test_adjoint_solve(oracle_mod, sphere02):
     lam, info = oracle_mod.gmres(M.transpose(), g, P, transpose=True, rtol=1e-13)
     assert info["status"] == 0
     assert np.linalg.norm(lam - lam_d) <= 1e-10 * np.linalg.norm(lam_d)
+
+
+# ------------------------------------------------------------------ two-level (coarse correction)
+# The paper leaves a coarse grid correction to future releases (Section 4.1.1);
+# the reading built here: coarse space Z with one constant per disjoint part,
+# E0 = Z^T M Z, applied multiplicatively before the one-level apply,
+# P2 = Q + P_RAS (I - M Q), Q = Z E0^{-1} Z^T.
+
+def test_coarse_matrix_row_sums_and_entries(oracle_mod, torus008):
+    """E0 = Z^T M Z: its row sums are c |part a| (M 1 = c 1), and every entry
+    equals a scipy product of the indicator matrix with M."""
+    B, M = torus008
+    P = oracle_mod.ORAS(B, M, 13, 2, coarse=True)
+    E = P.coarse_matrix()
+    part = P.partition()
+    sizes = np.bincount(part, minlength=13)
+    assert np.allclose(E.sum(axis=1), 10.0 * sizes, rtol=1e-12, atol=1e-9)
+    Z = sp.csr_matrix((np.ones(B.n_active), (np.arange(B.n_active), part)), shape=(B.n_active, 13))
+    want = (Z.T @ (M.to_scipy() @ Z)).toarray()
+    assert np.abs(E - want).max() <= 1e-12 * np.abs(want).max()
+
+
+def test_two_level_reproduces_the_coarse_space(oracle_mod, torus008):
+    """For v = Z c the coarse correction is exact and the one-level part sees
+    a zero residual: P2 (M Z c) = Z c (a wrong, transposed or incomplete E0
+    breaks it)."""
+    B, M = torus008
+    P = oracle_mod.ORAS(B, M, 13, 2, coarse=True)
+    part = P.partition()
+    c = inputs.gaussian_vector(71, 13)
+    v = c[part]
+    got = P.apply(M.matvec(v))
+    assert np.abs(got - v).max() <= 1e-10 * np.abs(v).max()
+
+
+def test_two_level_single_exact_subdomain_is_the_inverse(oracle_mod, sphere02):
+    """N_S = 1 with an exact local solve: P_RAS = M^{-1}, so
+    P2 = Q + M^{-1} (I - M Q) = M^{-1}."""
+    B, M = sphere02
+    P = oracle_mod.ORAS(B, M, 1, 0, exact=True, coarse=True)
+    r = inputs.gaussian_vector(72, B.n_active)
+    want = oracle_mod.dense_solve(M.to_scipy().toarray(), r)
+    assert np.abs(P.apply(r) - want).max() <= 1e-10 * np.abs(want).max()
+
+
+def test_two_level_transpose_is_the_adjoint(oracle_mod, torus008):
+    B, M = torus008
+    P = oracle_mod.ORAS(B, M, 13, 2, coarse=True)
+    x = inputs.gaussian_vector(73, B.n_active)
+    y = inputs.gaussian_vector(74, B.n_active)
+    lhs, rhs = np.dot(P.apply(x), y), np.dot(x, P.apply(y, transpose=True))
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+@pytest.fixture(scope="module")
+def torus008_direct(oracle_mod, torus008):
+    B, M = torus008
+    f = inputs.gaussian_vector(75, B.n_active)
+    lu = sla.splu(M.to_scipy().tocsc())
+    return B, M, f, lu.solve(f), lu.solve(f, trans="T")
+
+
+@pytest.mark.parametrize("robin", [False, True])
+def test_two_level_gmres_reaches_direct_solution_in_fewer_iterations(oracle_mod, torus008_direct, robin):
+    B, M, f, xd, ld = torus008_direct
+    MT = M.transpose()
+    its = {}
+    for coarse in (False, True):
+        P = oracle_mod.ORAS(B, M, 24, 2, robin=robin, order=oracle_mod.ORAS.LOCAL_SHELLS, coarse=coarse)
+        x, info = oracle_mod.gmres(M, f, P, rtol=1e-12)
+        assert np.linalg.norm(x - xd) <= 1e-9 * np.linalg.norm(xd)
+        its[coarse] = info["iters"]
+        lam, info = oracle_mod.gmres(MT, f, P, transpose=True, rtol=1e-12)
+        assert np.linalg.norm(lam - ld) <= 1e-9 * np.linalg.norm(ld)
+    assert its[True] < its[False], its
