@@ -463,7 +463,21 @@ def extras(torch, cpm, args, w, f, step, n, rtol):
                                                    mixed=True, reorth=0))
     out["bf16_factors"] = {"setup_s": tb_set, "solve_s": tb, "iters": ib["iters"], "status": ib["status"],
                            "rel_residual": ib["rel_residual"], "err_vs_reference": _rel(torch, ub, uref)}
-    del PB, B
+    del PB
+    # two-level preconditioner (coarse correction on one constant per part) at 512 and 2048 parts
+    two = {}
+    for parts in (512, 2048):
+        wp = dict(w, nparts=parts)
+        (P2, t_set) = _timed(torch, lambda: cpm.Schwarz(B, wp["c"], parts, wp["overlap"], robin=wp["robin"],
+                                                         store=cpm.CPM_F32, order=wp.get("order", 0), coarse=True))
+        (u2, i2), t2 = _timed(torch, lambda: cpm.solve(B, f, P2, rtol=rtol, restart=w["restart"], maxit=100000,
+                                                        mixed=True, reorth=0))
+        two[str(parts)] = {"setup_s": t_set, "solve_s": t2, "iters": i2["iters"], "status": i2["status"],
+                           "rel_residual": i2["rel_residual"], "err_vs_reference": _rel(torch, u2, uref),
+                           "solves_per_s_incl_setup": 1.0 / (t_set + t2)}
+        del P2
+    out["two_level"] = two
+    del B
     out["sphere_h0.1"] = sphere_case(torch, cpm)
     out["pipeline_h0.004"] = pipeline_h004(torch, cpm)
     return out

@@ -321,6 +321,9 @@ typedef struct {
   double delta1, delta2, lambda;  /* reaction parameters (eq. schnack) */
   double Du, Dv;                  /* diffusion coefficients, > 0 */
   double dt;                      /* step, > 0 */
+  int32_t model;                  /* 0 the Schnakenberg reaction; 1 no reaction: each
+                                     species follows the heat equation u_t = D Delta_S u
+                                     (Section 4.1.3) */
 } cpm_schnakenberg;
 
 /* cpm_imex_rhs -- right-hand sides of one step:
@@ -341,6 +344,23 @@ cpm_status cpm_imex_rhs(const cpm_band* band, const cpm_schnakenberg* prm, const
 cpm_status cpm_imex_rhs_adjoint(const cpm_band* band, const cpm_schnakenberg* prm, const double* u, const double* v,
                                 const double* u1, const double* v1, const double* lu, const double* lv,
                                 double* ubar, double* vbar, double* dc, void* stream);
+
+/* cpm_imex2_rhs -- right-hand sides of the two implicit stages of one
+ * second-order IMEX Runge-Kutta step, ARS(2,2,2) (Ascher, Ruuth & Spiteri
+ * 1997; the paper's reaction-diffusion and heat examples use PETSc's IMEX
+ * Runge-Kutta schemes, Section 4.1.3 and Section 4.1.5).  With
+ * gamma = 1 - 1/sqrt(2), delta = 1 - 1/(2 gamma), F = (f, g) the reaction and
+ * the shifts c_u = 1 / (gamma D_u dt), c_v = 1 / (gamma D_v dt), each stage
+ * solves M(c) U = b (cpm_solve with c = c_u, c_v):
+ *   stage 2:  bu = c_u (u + gamma dt f(u, v))
+ *   stage 3:  bu = c_u (u + dt (delta f(u, v) + (1 - delta) f(u2, v2))
+ *                      + ((1 - gamma) / gamma) (u2 - u - gamma dt f(u, v)))
+ * and likewise bv; the step's result is the stage-3 solution.
+ *   u, v     state at the start of the step; u2, v2 the stage-2 solutions
+ *            (stage 3 only; may be NULL for stage 2)
+ * All DEVICE, N_A doubles; bu, bv must not overlap the inputs. */
+cpm_status cpm_imex2_rhs(const cpm_band* band, const cpm_schnakenberg* prm, int32_t stage, const double* u,
+                         const double* v, const double* u2, const double* v2, double* bu, double* bv, void* stream);
 
 /* cpm_dot -- out[0] = <a, b> over N_A doubles (DEVICE a, b, out), in a fixed
  * reduction order.  Used by gradients with respect to the shift c

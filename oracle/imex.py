@@ -37,7 +37,10 @@ import scipy.sparse.linalg as sla
 
 
 def reaction(u, v, prm):
-    """f(u, v), g(u, v) of eq. schnack."""
+    """f(u, v), g(u, v) of eq. schnack; zero for model 1 (no reaction: the
+    heat equation u_t = D Delta_S u of Section 4.1.3 for each species)."""
+    if prm.get("model", 0) == 1:
+        return np.zeros_like(u), np.zeros_like(v)
     d1, d2, lam = prm["delta1"], prm["delta2"], prm["lambda"]
     f = d1 - u + u * u * v + lam * v
     g = d2 - u * u * v - lam * v
@@ -106,3 +109,56 @@ def steady_loss(states, prm):
     us, vs = steady_state(prm)
     u, v = states[-1]
     return 0.5 * float(np.sum((u - us) ** 2) + np.sum((v - vs) ** 2)), u - us, v - vs
+
+
+# ---------------------------------------------------------------------------
+# Second-order IMEX Runge-Kutta step, ARS(2,2,2) of Ascher, Ruuth & Spiteri
+# (1997): the paper integrates its reaction-diffusion and heat examples with
+# PETSc's IMEX Runge-Kutta schemes (Section 4.1.3, Section 4.1.5); this is a
+# second-order, L-stable member of that family.  With gamma = 1 - 1/sqrt(2),
+# delta = 1 - 1/(2 gamma), F the reaction (explicit) and G = D Delta_S the
+# diffusion (implicit):
+#
+#   U1 = u
+#   U2 = u + dt gamma F(U1) + dt gamma G(U2)
+#   U3 = u + dt (delta F(U1) + (1 - delta) F(U2)) + dt ((1 - gamma) G(U2) + gamma G(U3))
+#   u' = U3
+#
+# so each stage is one shifted Poisson solve with c = 1 / (gamma D dt):
+#   M(c) U2 = c (u + gamma dt F(U1))
+#   M(c) U3 = c (u + dt (delta F(U1) + (1 - delta) F(U2)) + (1 - gamma) dt G(U2)),
+# where dt G(U2) = (U2 - u - gamma dt F(U1)) / gamma follows from the first
+# equation (no operator apply needed).
+# ---------------------------------------------------------------------------
+ARS_GAMMA = 1.0 - 1.0 / np.sqrt(2.0)
+ARS_DELTA = 1.0 - 1.0 / (2.0 * ARS_GAMMA)
+
+
+class ImexArs2:
+    """ARS(2,2,2) steps of the two-species system on an oracle Band."""
+
+    def __init__(self, band, prm):
+        self.prm = dict(prm)
+        dt, g = prm["dt"], ARS_GAMMA
+        self.cu = 1.0 / (g * prm["Du"] * dt)
+        self.cv = 1.0 / (g * prm["Dv"] * dt)
+        self.lu_u = sla.splu(band.M(self.cu).to_scipy().tocsc())
+        self.lu_v = sla.splu(band.M(self.cv).to_scipy().tocsc())
+
+    def step(self, u, v):
+        dt, g, d = self.prm["dt"], ARS_GAMMA, ARS_DELTA
+        f1, g1 = reaction(u, v, self.prm)
+        u2 = self.lu_u.solve(self.cu * (u + g * dt * f1))
+        v2 = self.lu_v.solve(self.cv * (v + g * dt * g1))
+        f2, g2 = reaction(u2, v2, self.prm)
+        gu2 = (u2 - u - g * dt * f1) / g   # dt D_u Delta u2
+        gv2 = (v2 - v - g * dt * g1) / g
+        u3 = self.lu_u.solve(self.cu * (u + dt * (d * f1 + (1.0 - d) * f2) + (1.0 - g) * gu2))
+        v3 = self.lu_v.solve(self.cv * (v + dt * (d * g1 + (1.0 - d) * g2) + (1.0 - g) * gv2))
+        return u3, v3
+
+    def run(self, u0, v0, steps):
+        u, v = np.asarray(u0, dtype=np.float64).copy(), np.asarray(v0, dtype=np.float64).copy()
+        for _ in range(steps):
+            u, v = self.step(u, v)
+        return u, v

@@ -84,9 +84,12 @@ class Schnakenberg:
     species' solve (one per distinct c); solve_opts: rtol, restart, maxit, ...
     """
 
+    ARS_GAMMA = 1.0 - 0.5 ** 0.5  # implicit diagonal of ARS(2,2,2)
+
     def __init__(self, band, delta1=0.003, delta2=0.7, lam=0.06, dt=0.01, nparts=8, overlap=2, robin=False,
-                 **solve_opts):
+                 model=0, **solve_opts):
         self.band = band
+        self.model = int(model)  # 0 Schnakenberg reaction, 1 none (heat equation per species)
         self.delta1, self.delta2, self.lam, self.dt = float(delta1), float(delta2), float(lam), float(dt)
         self.nparts, self.overlap, self.robin = int(nparts), int(overlap), bool(robin)
         self.opts = dict(rtol=1e-10, maxit=20000)
@@ -101,7 +104,7 @@ class Schnakenberg:
 
     def params(self, Du, Dv):
         return {"delta1": self.delta1, "delta2": self.delta2, "lambda": self.lam, "Du": float(Du), "Dv": float(Dv),
-                "dt": self.dt}
+                "dt": self.dt, "model": self.model}
 
     def shifts(self, Du, Dv):
         return 1.0 / (float(Du) * self.dt), 1.0 / (float(Dv) * self.dt)
@@ -122,6 +125,31 @@ class Schnakenberg:
         v1 = _fwd_solve(self.band, self._pc(cv), cv, bv, self.opts, self.iters)
         self.solves += 2
         return u1, v1
+
+    def step_ars222(self, u, v, Du, Dv):
+        """One second-order IMEX Runge-Kutta step, ARS(2,2,2): two stages, each
+        one solve per species with c = 1 / (gamma D dt) (stage right-hand sides
+        by cpm_imex2_rhs).  Not differentiable (forward integration only)."""
+        prm = self.params(Du, Dv)
+        g = self.ARS_GAMMA
+        cu, cv = 1.0 / (g * float(Du) * self.dt), 1.0 / (g * float(Dv) * self.dt)
+        bu, bv = torch.empty_like(u), torch.empty_like(v)
+        cpm.cpm_imex2_rhs(self.band.handle, prm, 2, u, v, None, None, bu, bv)
+        u2 = _fwd_solve(self.band, self._pc(cu), cu, bu, self.opts, self.iters)
+        v2 = _fwd_solve(self.band, self._pc(cv), cv, bv, self.opts, self.iters)
+        cpm.cpm_imex2_rhs(self.band.handle, prm, 3, u, v, u2, v2, bu, bv)
+        u3 = _fwd_solve(self.band, self._pc(cu), cu, bu, self.opts, self.iters)
+        v3 = _fwd_solve(self.band, self._pc(cv), cv, bv, self.opts, self.iters)
+        self.solves += 4
+        return u3, v3
+
+    def integrate(self, u0, v0, Du, Dv, steps, scheme="ars222"):
+        """Forward integration without gradients: `scheme` is "euler"
+        (semi-implicit Euler) or "ars222" (second order)."""
+        u, v = u0.contiguous(), v0.contiguous()
+        for _ in range(int(steps)):
+            u, v = (self.step_ars222 if scheme == "ars222" else self.step)(u, v, float(Du), float(Dv))
+        return u, v
 
     def run(self, u0, v0, Du, Dv, steps, checkpoint=25):
         """(u_steps, v_steps) after `steps` steps from (u0, v0); differentiable

@@ -54,7 +54,7 @@ class cpm_solve_info(C.Structure):
 
 class cpm_schnakenberg(C.Structure):
     _fields_ = [("delta1", C.c_double), ("delta2", C.c_double), ("lambda_", C.c_double), ("Du", C.c_double),
-                ("Dv", C.c_double), ("dt", C.c_double)]
+                ("Dv", C.c_double), ("dt", C.c_double), ("model", C.c_int32)]
 
 
 class CpmError(RuntimeError):
@@ -96,6 +96,7 @@ def lib():
         "cpm_apply_noalloc": (i32, [vp, P(C.c_double), vp, vp, i32, i32, vp]),
         "cpm_imex_rhs": (i32, [vp, P(cpm_schnakenberg), vp, vp, vp, vp, vp]),
         "cpm_imex_rhs_adjoint": (i32, [vp, P(cpm_schnakenberg), vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
+        "cpm_imex2_rhs": (i32, [vp, P(cpm_schnakenberg), i32, vp, vp, vp, vp, vp, vp, vp]),
         "cpm_dot": (i32, [vp, vp, vp, vp, vp]),
         "cpm_solve_batch": (i32, [i32, vp, vp, P(C.c_double), P(C.c_int32), vp, vp, P(cpm_solve_params),
                                   P(cpm_solve_info), i32, vp]),
@@ -112,7 +113,8 @@ EXPORTED = ["cpm_last_error", "cpm_band_build", "cpm_band_info", "cpm_band_expor
             "oras_setup", "oras_apply", "oras_info", "oras_set_tuning", "oras_get_tuning", "oras_autotune",
             "oras_export", "cpm_solve",
             "cpm_solve_adjoint", "cpm_band_free", "oras_free", "cpm_kernel_launches", "cpm_device_allocations",
-            "cpm_apply_noalloc", "cpm_imex_rhs", "cpm_imex_rhs_adjoint", "cpm_dot", "cpm_solve_batch"]
+            "cpm_apply_noalloc", "cpm_imex_rhs", "cpm_imex_rhs_adjoint", "cpm_imex2_rhs", "cpm_dot",
+            "cpm_solve_batch"]
 
 
 def _check(st):
@@ -210,7 +212,14 @@ def oras_autotune(pc, dtype=CPM_F32, reps=3, stream=None):
 
 def _rx(prm):
     return cpm_schnakenberg(float(prm["delta1"]), float(prm["delta2"]), float(prm["lambda"]), float(prm["Du"]),
-                            float(prm["Dv"]), float(prm["dt"]))
+                            float(prm["Dv"]), float(prm["dt"]), int(prm.get("model", 0)))
+
+
+def cpm_imex2_rhs(band, prm, stage, u, v, u2, v2, bu, bv, stream=None):
+    """Right-hand sides of ARS(2,2,2) stage 2 (u2, v2 unused) or 3."""
+    _check(lib().cpm_imex2_rhs(band, C.byref(_rx(prm)), int(stage), _ptr(u), _ptr(v), _ptr(u2), _ptr(v2), _ptr(bu),
+                               _ptr(bv), _stream(stream)))
+    return bu, bv
 
 
 def cpm_imex_rhs(band, prm, u, v, bu, bv, stream=None):

@@ -278,6 +278,18 @@ struct Batch {
   float *x32 = nullptr, *y32 = nullptr;
   SysState X{};
   std::vector<void*> owned;
+  // CUDA graph of one cycle: a cycle is a fixed sequence of launches (systems
+  // stop on the device), so it is captured once per set of live problems and
+  // replayed; the first cycle of a solve runs uncaptured, since first uses
+  // (factor packing, transposed structures) synchronise.
+  cudaGraphExec_t cycle_exec = nullptr;
+  std::vector<char> cycle_live;
+  const double* cycle_x = nullptr;
+  bool cycle_f32 = false;
+  int cycle_inner = 0;
+  long long cycle_kernels = 0;  // kernels in the captured cycle (counted at each replay)
+  bool warm = false;
+  int graph_replays = 0, graph_captures = 0;
 
   template <typename T>
   cpm_status get(T** p, size_t n, cudaStream_t s) {
@@ -286,6 +298,8 @@ struct Batch {
     return CPM_OK;
   }
   void release(cudaStream_t s) {
+    if (cycle_exec) cudaGraphExecDestroy(cycle_exec);
+    cycle_exec = nullptr;
     for (void* p : owned) cudaFreeAsync(p, s);
     owned.clear();
     free_streams();
@@ -458,6 +472,47 @@ cpm_status batch_cycle(Batch& Bt, double* x, bool f32, int transpose, int maxit,
   return CPM_OK;
 }
 
+// One cycle through the graph cache: replay the captured cycle when the live
+// problems, the solution vector and the precision are those it was captured
+// with; otherwise capture this cycle (after one uncaptured warm-up cycle).
+cpm_status run_cycle(Batch& Bt, double* x, bool f32, int transpose, int maxit, double rtol, int inner,
+                     cudaStream_t s) {
+  if (Bt.cycle_exec && Bt.cycle_live == Bt.live && Bt.cycle_x == x && Bt.cycle_f32 == f32 &&
+      Bt.cycle_inner == inner) {
+    CPM_CUDA(cudaGraphLaunch(Bt.cycle_exec, s));
+    g_launches.fetch_add(Bt.cycle_kernels, std::memory_order_relaxed);
+    Bt.graph_replays++;
+    return CPM_OK;
+  }
+  if (!Bt.warm) {
+    Bt.warm = true;
+    return batch_cycle(Bt, x, f32, transpose, maxit, rtol, inner, s);
+  }
+  if (Bt.cycle_exec) cudaGraphExecDestroy(Bt.cycle_exec);
+  Bt.cycle_exec = nullptr;
+  const long long k0 = g_launches.load();
+  CPM_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  const cpm_status st = batch_cycle(Bt, x, f32, transpose, maxit, rtol, inner, s);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(s, &g);
+  if (st != CPM_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "capture of a batched GMRES cycle", __FILE__, __LINE__);
+  const cudaError_t e2 = cudaGraphInstantiate(&Bt.cycle_exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e2 != cudaSuccess) return cuda_fail(e2, "instantiation of a batched GMRES cycle", __FILE__, __LINE__);
+  Bt.cycle_kernels = g_launches.load() - k0;
+  Bt.cycle_live = Bt.live;
+  Bt.cycle_x = x;
+  Bt.cycle_f32 = f32;
+  Bt.cycle_inner = inner;
+  Bt.graph_captures++;
+  CPM_CUDA(cudaGraphLaunch(Bt.cycle_exec, s));
+  return CPM_OK;
+}
+
 }  // namespace
 
 cpm_status solve_batch(int nprob, const cpm_band* const* bands, const oras_pc* const* pcs, const double* c,
@@ -582,7 +637,7 @@ cpm_status solve_batch(int nprob, const cpm_band* const* bands, const oras_pc* c
       }
     ++cycles;
     if (!mixed) {
-      BTRY(batch_cycle(Bt, u, false, transpose, prm->maxit, prm->rtol, 0, s));
+      BTRY(run_cycle(Bt, u, false, transpose, prm->maxit, prm->rtol, 0, s));
     } else {
       // refinement step: systems already at rtol get no correction (their
       // residual is zeroed, which freezes them in the inner cycle)
@@ -594,7 +649,7 @@ cpm_status solve_batch(int nprob, const cpm_band* const* bands, const oras_pc* c
                : CPM_ERR_CUDA);
       KL(kb_scale<<<Bt.NB, RED_THREADS, 0, s>>>(Bt.G, Bt.r, X.scale, Bt.r));
       BTRY(cudaMemsetAsync(d, 0, Bt.N * sizeof(double), s) == cudaSuccess ? CPM_OK : CPM_ERR_CUDA);
-      BTRY(batch_cycle(Bt, d, true, transpose, prm->maxit, inner, 1, s));
+      BTRY(run_cycle(Bt, d, true, transpose, prm->maxit, inner, 1, s));
       KL(kb_axpy<<<grid_n(Bt.N), 256, 0, s>>>(d, u, Bt.N));
       BTRY(cudaStreamSynchronize(s) == cudaSuccess ? CPM_OK : CPM_ERR_CUDA);  // keep is read by the copy
     }

@@ -213,6 +213,7 @@ static cpm_status check_rx(const cpm_schnakenberg* p) {
   if (!std::isfinite(p->delta1) || !std::isfinite(p->delta2) || !std::isfinite(p->lambda) || !std::isfinite(p->Du) ||
       !std::isfinite(p->Dv) || !std::isfinite(p->dt))
     return fail(CPM_ERR_NAN, "reaction parameters must be finite");
+  if (p->model != 0 && p->model != 1) return fail(CPM_ERR_ARG, "model must be 0 (Schnakenberg) or 1 (no reaction)");
   return CPM_OK;
 }
 
@@ -222,6 +223,20 @@ cpm_status cpm_imex_rhs(const cpm_band* band, const cpm_schnakenberg* prm, const
   if (bu == u || bu == v || bv == u || bv == v || bu == bv) return fail(CPM_ERR_ARG, "outputs must not alias inputs");
   CPM_TRY(check_rx(prm));
   return imex_rhs(prm, band->nA, u, v, bu, bv, as_stream(stream));
+}
+
+cpm_status cpm_imex2_rhs(const cpm_band* band, const cpm_schnakenberg* prm, int32_t stage, const double* u,
+                         const double* v, const double* u2, const double* v2, double* bu, double* bv, void* stream) {
+  if (!band || !u || !v || !bu || !bv) return fail(CPM_ERR_ARG, "null argument");
+  if (stage != 2 && stage != 3) return fail(CPM_ERR_ARG, "stage must be 2 or 3");
+  if (stage == 3 && (!u2 || !v2)) return fail(CPM_ERR_ARG, "stage 3 needs the stage-2 solutions");
+  const size_t bytes = (size_t)band->nA * sizeof(double);
+  for (const double* in : {u, v, u2, v2})
+    if (in && (ranges_overlap(in, bu, bytes) || ranges_overlap(in, bv, bytes)))
+      return fail(CPM_ERR_ARG, "outputs must not overlap the inputs");
+  if (ranges_overlap(bu, bv, bytes)) return fail(CPM_ERR_ARG, "bu and bv must not overlap");
+  CPM_TRY(check_rx(prm));
+  return imex2_rhs(prm, stage, band->nA, u, v, u2, v2, bu, bv, as_stream(stream));
 }
 
 cpm_status cpm_imex_rhs_adjoint(const cpm_band* band, const cpm_schnakenberg* prm, const double* u, const double* v,

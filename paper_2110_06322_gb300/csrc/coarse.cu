@@ -31,8 +31,8 @@ cpm_status oras_run_one_level(const oras_pc* P, const void* r, void* z, cpm_dtyp
 
 namespace {
 
-constexpr int KMZ = 16;    // most parts one matrix row may reach
-constexpr int NBMAX = 64;  // most parts one part's rows may reach
+constexpr int KMZ = 64;    // most parts one matrix row may reach (a row spans a few lattice cells)
+constexpr int NBMAX = 64;  // parts one part's rows reach, summed warp-parallel (more: by one lane)
 
 // rows of M Z: for node i, the distinct parts of its row's columns (in order
 // of first appearance along the ascending columns) and the row's sum over
@@ -108,13 +108,23 @@ __global__ void __launch_bounds__(32) k_coarse_e0(int np, const int64_t* __restr
         ++k;
       }
     }
-    if (k > NBMAX) atomicExch(err, CPM_ERR_ARG);
-    nn = k < NBMAX ? k : NBMAX;
+    nn = k;
   }
   __syncwarp();
   const int n = nn;
   if (n == 0) {  // an empty part: a decoupled unit row keeps E0 regular (its Z^T r is 0)
     if (lane == 0) E0[(int64_t)a * np + a] = 1.0;
+    return;
+  }
+  if (n > NBMAX) {
+    // a small part among many tiny ones reaches more parts than there are
+    // slots: one lane sums its rows in order straight into the zeroed E0 row
+    if (lane == 0)
+      for (int64_t q = b0; q < b1; ++q)
+        if (owned[q]) {
+          const int64_t i = snode[q];
+          for (int64_t e = mzptr[i]; e < mzptr[i + 1]; ++e) E0[(int64_t)a * np + mzpart[e]] += mzval[e];
+        }
     return;
   }
   for (int64_t q = b0 + lane; q < b1; q += 32)
@@ -370,8 +380,7 @@ cpm_status coarse_build(oras_pc* P, const int64_t* mptr, const int32_t* mcol, co
   int herr = 0;
   CPM_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
   CPM_CUDA(cudaStreamSynchronize(s));
-  if (herr) return done(fail(CPM_ERR_ARG, "a part reaches more than %d parts: the coarse structure does not fit",
-                             NBMAX));
+  if (herr) return done(fail(CPM_ERR_ARG, "a matrix row reaches more than %d parts", KMZ));
   const int GE = grid_for(nn, 256);
   KL(k_eye<<<GE, 256, 0, s>>>(np, P->E0inv));
   for (int k = 0; k < np; ++k) {

@@ -27,12 +27,19 @@ constexpr int IMX_BLOCKS = 152 * 4;  // fixed grid: the dL/dc sums are reproduci
 
 struct Rx {
   double d1, d2, lam, dt, cu, cv;
+  int model;  // 0 Schnakenberg reaction, 1 none (heat equation)
 };
 
 __device__ __forceinline__ double rx_f(const Rx& R, double u, double v) {
-  return R.d1 - u + u * u * v + R.lam * v;
+  return R.model ? 0.0 : R.d1 - u + u * u * v + R.lam * v;
 }
-__device__ __forceinline__ double rx_g(const Rx& R, double u, double v) { return R.d2 - u * u * v - R.lam * v; }
+__device__ __forceinline__ double rx_g(const Rx& R, double u, double v) {
+  return R.model ? 0.0 : R.d2 - u * u * v - R.lam * v;
+}
+
+// ARS(2,2,2) coefficients (gamma = 1 - 1/sqrt(2), delta = 1 - 1/(2 gamma))
+constexpr double ARS_G = 0.29289321881345247560;
+constexpr double ARS_D = -0.70710678118654752440;
 
 __global__ void __launch_bounds__(IMX_THREADS)
     k_imex_rhs(Rx R, int64_t n, const double* __restrict__ u, const double* __restrict__ v, double* bu, double* bv) {
@@ -40,6 +47,27 @@ __global__ void __launch_bounds__(IMX_THREADS)
     const double ui = u[i], vi = v[i];
     bu[i] = R.cu * (ui + R.dt * rx_f(R, ui, vi));
     bv[i] = R.cv * (vi + R.dt * rx_g(R, ui, vi));
+  }
+}
+
+// stage right-hand sides of one ARS(2,2,2) step (R.cu, R.cv: 1 / (gamma D dt))
+__global__ void __launch_bounds__(IMX_THREADS)
+    k_imex2_rhs(Rx R, int stage, int64_t n, const double* __restrict__ u, const double* __restrict__ v,
+                const double* __restrict__ u2, const double* __restrict__ v2, double* bu, double* bv) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double ui = u[i], vi = v[i];
+    const double f1 = rx_f(R, ui, vi), g1 = rx_g(R, ui, vi);
+    if (stage == 2) {
+      bu[i] = R.cu * (ui + ARS_G * R.dt * f1);
+      bv[i] = R.cv * (vi + ARS_G * R.dt * g1);
+    } else {
+      const double a = u2[i], b = v2[i];
+      const double f2 = rx_f(R, a, b), g2 = rx_g(R, a, b);
+      const double gu2 = (a - ui - ARS_G * R.dt * f1) / ARS_G;  // dt D_u Delta u2
+      const double gv2 = (b - vi - ARS_G * R.dt * g1) / ARS_G;
+      bu[i] = R.cu * (ui + R.dt * (ARS_D * f1 + (1.0 - ARS_D) * f2) + (1.0 - ARS_G) * gu2);
+      bv[i] = R.cv * (vi + R.dt * (ARS_D * g1 + (1.0 - ARS_D) * g2) + (1.0 - ARS_G) * gv2);
+    }
   }
 }
 
@@ -65,7 +93,8 @@ __global__ void __launch_bounds__(IMX_THREADS)
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double ui = u[i], vi = v[i], a = lu[i], b = lv[i];
     const double uv = ui * vi, uu = ui * ui;
-    const double fu = -1.0 + 2.0 * uv, fv = uu + R.lam, gu = -2.0 * uv, gv = -uu - R.lam;
+    const double fu = R.model ? 0.0 : -1.0 + 2.0 * uv, fv = R.model ? 0.0 : uu + R.lam;
+    const double gu = R.model ? 0.0 : -2.0 * uv, gv = R.model ? 0.0 : -uu - R.lam;
     ubar[i] = R.cu * a * (1.0 + R.dt * fu) + R.cv * b * (R.dt * gu);
     vbar[i] = R.cu * a * (R.dt * fv) + R.cv * b * (1.0 + R.dt * gv);
     su += a * (ui + R.dt * rx_f(R, ui, vi) - u1[i]);
@@ -108,6 +137,7 @@ Rx make_rx(const cpm_schnakenberg* p) {
   R.dt = p->dt;
   R.cu = 1.0 / (p->Du * p->dt);
   R.cv = 1.0 / (p->Dv * p->dt);
+  R.model = p->model;
   return R;
 }
 
@@ -116,6 +146,16 @@ Rx make_rx(const cpm_schnakenberg* p) {
 cpm_status imex_rhs(const cpm_schnakenberg* prm, int64_t n, const double* u, const double* v, double* bu, double* bv,
                     cudaStream_t s) {
   KL(k_imex_rhs<<<grid_for(n, IMX_THREADS), IMX_THREADS, 0, s>>>(make_rx(prm), n, u, v, bu, bv));
+  CPM_CUDA(cudaGetLastError());
+  return CPM_OK;
+}
+
+cpm_status imex2_rhs(const cpm_schnakenberg* prm, int stage, int64_t n, const double* u, const double* v,
+                     const double* u2, const double* v2, double* bu, double* bv, cudaStream_t s) {
+  Rx R = make_rx(prm);
+  R.cu = 1.0 / (ARS_G * prm->Du * prm->dt);
+  R.cv = 1.0 / (ARS_G * prm->Dv * prm->dt);
+  KL(k_imex2_rhs<<<grid_for(n, IMX_THREADS), IMX_THREADS, 0, s>>>(R, stage, n, u, v, u2, v2, bu, bv));
   CPM_CUDA(cudaGetLastError());
   return CPM_OK;
 }

@@ -39,6 +39,8 @@ cpm_status solve_batch(int nprob, const cpm_band* const* bands, const oras_pc* c
 // imex.cu: reaction-diffusion step right-hand sides, their adjoint, dot product
 cpm_status imex_rhs(const cpm_schnakenberg* prm, int64_t n, const double* u, const double* v, double* bu, double* bv,
                     cudaStream_t s);
+cpm_status imex2_rhs(const cpm_schnakenberg* prm, int stage, int64_t n, const double* u, const double* v,
+                     const double* u2, const double* v2, double* bu, double* bv, cudaStream_t s);
 cpm_status imex_rhs_adjoint(const cpm_schnakenberg* prm, int64_t n, const double* u, const double* v,
                             const double* u1, const double* v1, const double* lu, const double* lv, double* ubar,
                             double* vbar, double* dc, cudaStream_t s);

@@ -17,7 +17,7 @@ STRUCTS = {
     "cpm_solve_params": ["restart", "maxit", "rtol", "mixed", "reorth", "inner_rtol", "timing"],
     "cpm_solve_info": ["iters", "restarts", "ir_steps", "rel_residual", "status", "ms_precond", "ms_operator",
                        "n_precond", "n_operator"],
-    "cpm_schnakenberg": ["delta1", "delta2", "lambda", "Du", "Dv", "dt"],
+    "cpm_schnakenberg": ["delta1", "delta2", "lambda", "Du", "Dv", "dt", "model"],
 }
 PY_NAME = {("cpm_schnakenberg", "lambda"): "lambda_"}
 

@@ -179,3 +179,32 @@ def test_imex_rhs_adjoint_accumulates(cpm, sphere):
     cpm.cpm_dot(B.handle, x[0], x[1], out)
     ref = float(np.dot(x[0].cpu().numpy(), x[1].cpu().numpy()))
     assert abs(out.item() - ref) <= 1e-12 * np.linalg.norm(x[0].cpu().numpy()) * np.linalg.norm(x[1].cpu().numpy())
+
+
+@pytest.mark.parametrize("model", [0, 1])
+def test_ars222_steps_match_oracle(cpm, ag, oracle_mod, sphere, model):
+    """Second-order IMEX steps (ARS(2,2,2)) on the GPU against the oracle's
+    steps with sparse direct solves: Schnakenberg (model 0) and the heat
+    equation per species (model 1), four steps, states to 1e-10 relative."""
+    B, O = sphere
+    prm = dict(PRM, model=model)
+    n = B.n_active
+    u0, v0 = _ic(n, 41, 0.2)
+    sim = ag.Schnakenberg(B, dt=prm["dt"], nparts=8, overlap=2, model=model, **TIGHT)
+    u, v = sim.integrate(_cuda(u0), _cuda(v0), prm["Du"], prm["Dv"], 4, scheme="ars222")
+    wu, wv = oimex.ImexArs2(O, prm).run(u0, v0, 4)
+    assert np.abs(u.cpu().numpy() - wu).max() <= 1e-10 * np.abs(wu).max()
+    assert np.abs(v.cpu().numpy() - wv).max() <= 1e-10 * np.abs(wv).max()
+    assert sim.solves == 16
+
+
+def test_euler_heat_model_matches_oracle(cpm, ag, oracle_mod, sphere):
+    """The first-order step with no reaction (heat equation) against the oracle."""
+    B, O = sphere
+    prm = dict(PRM, model=1)
+    u0, v0 = _ic(B.n_active, 43, 0.2)
+    sim = ag.Schnakenberg(B, dt=prm["dt"], nparts=8, overlap=2, model=1, **TIGHT)
+    u, v = sim.integrate(_cuda(u0), _cuda(v0), prm["Du"], prm["Dv"], 3, scheme="euler")
+    wu, wv = oimex.Imex(O, prm).run(u0, v0, 3)[-1]
+    assert np.abs(u.cpu().numpy() - wu).max() <= 1e-10 * np.abs(wu).max()
+    assert np.abs(v.cpu().numpy() - wv).max() <= 1e-10 * np.abs(wv).max()
