@@ -237,6 +237,8 @@ struct Batch {
   // iteration run concurrently (small problems fill only a few SMs each)
   static constexpr int NSTREAM = 8;
   cudaStream_t ss[NSTREAM] = {};
+  cudaStream_t cap = nullptr;  // private stream the cycle graph is captured on (the caller's
+                               // stream may be the legacy default stream, which cannot capture)
   cudaEvent_t fork = nullptr, join[NSTREAM] = {};
   cpm_status make_streams() {
     for (int k = 0; k < NSTREAM; ++k) {
@@ -244,6 +246,7 @@ struct Batch {
       CPM_CUDA(cudaEventCreateWithFlags(&join[k], cudaEventDisableTiming));
     }
     CPM_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    CPM_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
     return CPM_OK;
   }
   void free_streams() {
@@ -255,6 +258,8 @@ struct Batch {
     }
     if (fork) cudaEventDestroy(fork);
     fork = nullptr;
+    if (cap) cudaStreamDestroy(cap);
+    cap = nullptr;
   }
   // side streams start after everything queued on s so far
   cpm_status fan_out(cudaStream_t s) {
@@ -475,6 +480,7 @@ cpm_status batch_cycle(Batch& Bt, double* x, bool f32, int transpose, int maxit,
 // One cycle through the graph cache: replay the captured cycle when the live
 // problems, the solution vector and the precision are those it was captured
 // with; otherwise capture this cycle (after one uncaptured warm-up cycle).
+// Capture runs on the batch's private stream; the graph is launched on s.
 cpm_status run_cycle(Batch& Bt, double* x, bool f32, int transpose, int maxit, double rtol, int inner,
                      cudaStream_t s) {
   if (Bt.cycle_exec && Bt.cycle_live == Bt.live && Bt.cycle_x == x && Bt.cycle_f32 == f32 &&
@@ -491,10 +497,10 @@ cpm_status run_cycle(Batch& Bt, double* x, bool f32, int transpose, int maxit, d
   if (Bt.cycle_exec) cudaGraphExecDestroy(Bt.cycle_exec);
   Bt.cycle_exec = nullptr;
   const long long k0 = g_launches.load();
-  CPM_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-  const cpm_status st = batch_cycle(Bt, x, f32, transpose, maxit, rtol, inner, s);
+  CPM_CUDA(cudaStreamBeginCapture(Bt.cap, cudaStreamCaptureModeThreadLocal));
+  const cpm_status st = batch_cycle(Bt, x, f32, transpose, maxit, rtol, inner, Bt.cap);
   cudaGraph_t g = nullptr;
-  const cudaError_t e = cudaStreamEndCapture(s, &g);
+  const cudaError_t e = cudaStreamEndCapture(Bt.cap, &g);
   if (st != CPM_OK) {
     if (g) cudaGraphDestroy(g);
     return st;

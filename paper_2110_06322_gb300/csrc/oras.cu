@@ -1094,15 +1094,16 @@ cpm_status oras_build(const cpm_band* B, const oras_params* prm, double c, cudaS
   TRYC(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
   TRYC(cudaStreamSynchronize(s));
   if (herr) return cleanup(fail(CPM_ERR_BREAKDOWN, "zero pivot in the ILU(0) factorisation"));
-  // level-packed factors for the applies: FP64, and the stored precision
+  // level-packed factors for the applies in the stored precision; the FP64
+  // stream is packed on the first FP64 apply (mixed-precision solves never
+  // need it, and it is the largest copy of the factors)
   TRY(dalloc(&P->err, 1, s));
   TRYC(cudaMemsetAsync(P->err, 0, sizeof(int), s));
   {
-    const cpm_dtype vts[2] = {CPM_F64, (cpm_dtype)P->store};
-    PackedFactors tmp[2];
-    TRY(pack_factors(P, 0, vts, tmp, P->store != CPM_F64 ? 2 : 1, s));
-    P->packed[0] = tmp[0];
-    P->packed[1] = tmp[1];
+    const cpm_dtype vt = (cpm_dtype)P->store;
+    PackedFactors tmp;
+    TRY(pack_factors(P, 0, &vt, &tmp, 1, s));
+    P->packed[vt == CPM_F64 ? 0 : 1] = tmp;
   }
   TRYC(cudaGetLastError());
 #undef TRY

@@ -678,12 +678,25 @@ static cpm_status allow_pk_smem(cudaStream_t) {
   return CPM_OK;
 }
 
-template <typename T, typename V, bool SMEMX>
-static void launch_pk(int lanes, dim3 g, size_t sm, cudaStream_t s, const PkArgs& A, const T* r, T* z, T* xl) {
+// Shared-memory carve-out of the one-CTA-per-SM mode (percent of the largest
+// carve-out: 28 % is the 64 KB configuration) and the dynamic shared memory
+// it requests so that a second CTA cannot fit beside the first.
+constexpr int PK_CARVE_ONE = 28;
+constexpr size_t PK_SMEM_ONE = 60 * 1024;
+
+template <typename T, typename V, bool SMEMX, int L>
+static void launch_pk_l(int carve, dim3 g, size_t sm, cudaStream_t s, const PkArgs& A, const T* r, T* z, T* xl) {
   constexpr int NT = (PK_WARPS + 1) * 32;
-  if (lanes == 4) KL(k_schwarz_pk<T, V, SMEMX, 4><<<g, NT, sm, s>>>(A, r, z, xl));
-  else if (lanes == 16) KL(k_schwarz_pk<T, V, SMEMX, 16><<<g, NT, sm, s>>>(A, r, z, xl));
-  else KL(k_schwarz_pk<T, V, SMEMX, 8><<<g, NT, sm, s>>>(A, r, z, xl));
+  cudaFuncSetAttribute(k_schwarz_pk<T, V, SMEMX, L>, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
+  KL(k_schwarz_pk<T, V, SMEMX, L><<<g, NT, sm, s>>>(A, r, z, xl));
+}
+
+template <typename T, typename V, bool SMEMX>
+static void launch_pk(int lanes, int carve, dim3 g, size_t sm, cudaStream_t s, const PkArgs& A, const T* r, T* z,
+                      T* xl) {
+  if (lanes == 4) launch_pk_l<T, V, SMEMX, 4>(carve, g, sm, s, A, r, z, xl);
+  else if (lanes == 16) launch_pk_l<T, V, SMEMX, 16>(carve, g, sm, s, A, r, z, xl);
+  else launch_pk_l<T, V, SMEMX, 8>(carve, g, sm, s, A, r, z, xl);
 }
 
 template <typename T, typename V>
@@ -711,7 +724,11 @@ static cpm_status run_pk(const oras_pc* P, const PackedFactors& pf, const T* r, 
   // local vector in shared memory when it fits beside the ring with two CTAs
   // per SM, unless the caller asked for the global slice
   const bool smemx = P->xplace == 0 && ring + xsb <= 113 * 1024;
-  const size_t sm = smemx ? ring + xsb : ring;
+  // one CTA per SM with a small shared-memory carve-out (the rest of the SM's
+  // memory is L1, which then holds most of one subdomain's global slice)
+  const bool one_cta = !smemx && P->l1 == 1 && ring <= PK_SMEM_ONE;
+  const size_t sm = smemx ? ring + xsb : (one_cta ? PK_SMEM_ONE : ring);
+  const int carve = one_cta ? PK_CARVE_ONE : (int)cudaSharedmemCarveoutDefault;
   if (sm > PK_SMEM_MAX) return fail(CPM_ERR_ARG, "Schwarz apply needs %zu bytes of shared memory", sm);
   CPM_TRY((allow_pk_smem<T, V>(s)));
   T* xloc = nullptr;
@@ -721,8 +738,10 @@ static cpm_status run_pk(const oras_pc* P, const PackedFactors& pf, const T* r, 
     dim3 g(P->np, nr);
     T* xl = xloc ? xloc + (int64_t)r0 * P->nloc : nullptr;
     const int lanes = P->lanes ? P->lanes : (smemx ? SW_LPR_SMEM : SW_LPR_GLOBAL);
-    if (smemx) launch_pk<T, V, true>(lanes, g, sm, s, A, r + (int64_t)r0 * P->nA, z + (int64_t)r0 * P->nA, xl);
-    else launch_pk<T, V, false>(lanes, g, sm, s, A, r + (int64_t)r0 * P->nA, z + (int64_t)r0 * P->nA, xl);
+    if (smemx)
+      launch_pk<T, V, true>(lanes, carve, g, sm, s, A, r + (int64_t)r0 * P->nA, z + (int64_t)r0 * P->nA, xl);
+    else
+      launch_pk<T, V, false>(lanes, carve, g, sm, s, A, r + (int64_t)r0 * P->nA, z + (int64_t)r0 * P->nA, xl);
     if (transpose) {
       dim3 g2(grid_for(P->nA, 256), nr);
       KL(k_gather_T2<T><<<g2, 256, 0, s>>>(P->nA, P->nloc, P->mcnt, P->mloc, xl, z + (int64_t)r0 * P->nA));
@@ -759,15 +778,21 @@ cpm_status oras_tune(oras_pc* P, cpm_dtype dt, int reps, cudaStream_t s, oras_tu
   if (cudaMemsetAsync(r, 0, P->nA * esz, s) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
       cudaEventCreate(&e1) != cudaSuccess)
     return done(fail(CPM_ERR_CUDA, "autotune set-up failed"));
-  oras_tuning keep{P->xplace, P->lanes, P->schedule, 0, P->wait_polls}, win = keep;
+  oras_tuning keep{P->xplace, P->lanes, P->schedule, P->l1, 0, P->wait_polls}, win = keep;
   double win_ms = 1e300;
   const int lanes[3] = {4, 8, 16};
+  if ((st = oras_run(P, r, z, dt, 1, 0, s)) != CPM_OK) return done(st);  // packs this precision if needed
+  const size_t ring = (size_t)NSTAGE * CHUNK_BYTES + pad16(2 * P->packed[dt == CPM_F64 ? 0 : 1].max_chunks);
+  const bool fits = ring + (size_t)P->max_rows * esz <= PK_SMEM_MAX;
   for (int xp = 0; xp < 2; ++xp)
     for (int li = 0; li < 3; ++li)
-      for (int sc = 0; sc < 2; ++sc) {
+      for (int sc = 0; sc < 2; ++sc)
+        for (int l1 = 0; l1 < 2; ++l1) {
+        if (l1 == 1 && xp == 0 && fits) continue;  // l1 only matters for global slices
         P->xplace = xp;
         P->lanes = lanes[li];
         P->schedule = sc;
+        P->l1 = l1;
         if ((st = oras_run(P, r, z, dt, 1, 0, s)) != CPM_OK) return done(st);  // warm-up (packs on first use)
         cudaEventRecord(e0, s);
         for (int q = 0; q < reps; ++q)
@@ -778,18 +803,20 @@ cpm_status oras_tune(oras_pc* P, cpm_dtype dt, int reps, cudaStream_t s, oras_tu
         cudaEventElapsedTime(&ms, e0, e1);
         if (ms / reps < win_ms) {
           win_ms = ms / reps;
-          win = oras_tuning{xp, lanes[li], sc, 0, keep.wait_polls};
+          win = oras_tuning{xp, lanes[li], sc, l1, 0, keep.wait_polls};
         }
       }
   if ((st = oras_take_error(P, s)) != CPM_OK) {
     P->xplace = keep.xplace;
     P->lanes = keep.lanes;
     P->schedule = keep.schedule;
+    P->l1 = keep.l1;
     return done(st);
   }
   P->xplace = win.xplace;
   P->lanes = win.lanes;
   P->schedule = win.schedule;
+  P->l1 = win.l1;
   if (best) *best = win;
   if (best_ms) *best_ms = win_ms;
   return done(CPM_OK);

@@ -108,7 +108,7 @@ def test_apply_wrappers_check_their_vectors(lib):
 
 def test_tuning_arguments_are_rejected(lib):
     from paper_2110_06322_gb300 import cpm
-    t = cpm.oras_tuning(0, 0, 0, 0, 0)
+    t = cpm.oras_tuning(0, 0, 0, 0, 0, 0)
     assert lib.oras_set_tuning(None, C.byref(t)) == cpm.CPM_ERR_ARG
     assert lib.oras_get_tuning(None, C.byref(t)) == cpm.CPM_ERR_ARG
     assert lib.oras_autotune(None, cpm.CPM_F32, 3, None, None, None) == cpm.CPM_ERR_ARG
