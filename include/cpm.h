@@ -199,10 +199,11 @@ cpm_status oras_apply(const oras_pc* pc, const void* r, void* z, cpm_dtype dtype
  *                  slice)
  *   schedule       order in which subdomains are handed to CTAs: 0 longest
  *                  first (default), 1 partition order
- *   l1             with the local vector in a global slice: 0 two CTAs per SM
- *                  (default); 1 one CTA per SM with a 64 KB shared-memory
- *                  carve-out, which leaves the rest of the SM's 256 KB to the L1
- *                  cache that holds the slice
+ *   ctas           CTAs per SM when the local vectors live in global slices: 0
+ *                  two (default); 1 one, with a 64 KB shared-memory carve-out that
+ *                  leaves the rest of the SM's 256 KB to the L1 cache holding the
+ *                  slice; 4 four, of 6 consumer warps each (8 lanes per row), so
+ *                  that up to 608 subdomains run at once
  *   probe_timeout  0 normal; 1 failure-path test: the first factor-chunk wait
  *                  of every subdomain waits on a barrier that nothing completes,
  *                  so each CTA runs out after wait_polls polls, waits for its
@@ -216,7 +217,7 @@ typedef struct {
   int32_t xplace;
   int32_t lanes;
   int32_t schedule;
-  int32_t l1;
+  int32_t ctas;
   int32_t probe_timeout;
   int64_t wait_polls;
 } oras_tuning;
@@ -224,8 +225,8 @@ cpm_status oras_set_tuning(oras_pc* pc, const oras_tuning* t);
 cpm_status oras_get_tuning(const oras_pc* pc, oras_tuning* t);
 
 /* oras_autotune -- time every combination of xplace (both when the local
- * vectors fit in shared memory), lanes (4, 8, 16), schedule (0, 1) and l1
- * (0, 1; where the local vectors live in global slices) on
+ * vectors fit in shared memory), lanes (4, 8, 16), schedule (0, 1) and ctas
+ * (0, 1, 4; where the local vectors live in global slices) on
  * `reps` forward applies of dtype (CPM_F32 or CPM_F64) each, with CUDA events
  * on `stream`, and keep the fastest as the preconditioner's setting (the
  * probe stays off).  best (HOST, may be NULL) receives it and best_ms (HOST,

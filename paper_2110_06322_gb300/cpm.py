@@ -37,7 +37,7 @@ class oras_params(C.Structure):
 
 
 class oras_tuning(C.Structure):
-    _fields_ = [("xplace", C.c_int32), ("lanes", C.c_int32), ("schedule", C.c_int32), ("l1", C.c_int32),
+    _fields_ = [("xplace", C.c_int32), ("lanes", C.c_int32), ("schedule", C.c_int32), ("ctas", C.c_int32),
                 ("probe_timeout", C.c_int32), ("wait_polls", C.c_int64)]
 
 
@@ -186,13 +186,13 @@ def cpm_device_allocations():
     return lib().cpm_device_allocations()
 
 
-def oras_set_tuning(pc, xplace=0, lanes=0, schedule=0, probe_timeout=0, wait_polls=0, l1=0):
-    t = oras_tuning(int(xplace), int(lanes), int(schedule), int(l1), int(probe_timeout), int(wait_polls))
+def oras_set_tuning(pc, xplace=0, lanes=0, schedule=0, probe_timeout=0, wait_polls=0, ctas=0):
+    t = oras_tuning(int(xplace), int(lanes), int(schedule), int(ctas), int(probe_timeout), int(wait_polls))
     _check(lib().oras_set_tuning(pc, C.byref(t)))
 
 
 def _tuning_dict(t):
-    return {"xplace": t.xplace, "lanes": t.lanes, "schedule": t.schedule, "l1": t.l1,
+    return {"xplace": t.xplace, "lanes": t.lanes, "schedule": t.schedule, "ctas": t.ctas,
             "probe_timeout": t.probe_timeout, "wait_polls": t.wait_polls}
 
 
@@ -378,11 +378,11 @@ class Schwarz:
         z = torch.empty_like(r) if out is None else out
         return oras_apply(self.handle, r, z, self.band.n_active, transpose, stream)
 
-    def set_tuning(self, xplace=0, lanes=0, schedule=0, probe_timeout=0, wait_polls=0, l1=0):
+    def set_tuning(self, xplace=0, lanes=0, schedule=0, probe_timeout=0, wait_polls=0, ctas=0):
         """Run-time settings of the apply (oras_set_tuning): local-vector
         placement, lanes per factor row, subdomain schedule, CTAs per SM
         for global slices, the failure-path probe and the wait bound."""
-        oras_set_tuning(self.handle, xplace, lanes, schedule, probe_timeout, wait_polls, l1)
+        oras_set_tuning(self.handle, xplace, lanes, schedule, probe_timeout, wait_polls, ctas)
 
     def tuning(self):
         return oras_get_tuning(self.handle)

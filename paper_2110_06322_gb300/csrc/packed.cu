@@ -43,7 +43,8 @@ namespace {
 
 constexpr int CHUNK_BYTES = 24576;
 constexpr int NSTAGE = 2;
-constexpr int PK_WARPS = 12;
+constexpr int PK_WARPS = 12;       // consumer warps of a CTA (two CTAs per SM)
+constexpr int PK_WARPS_FOUR = 6;   // consumer warps in the four-CTAs-per-SM mode (global slices)
 constexpr unsigned WAIT_LIMIT = 1u << 22;  // polls of one mbarrier before giving up (seconds at most)
 
 __host__ __device__ inline int64_t pad16(int64_t b) { return (b + 15) & ~(int64_t)15; }
@@ -416,18 +417,20 @@ struct PkArgs {
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
-// barrier among the consumer warps only (named barrier 1)
+// barrier among the NW consumer warps only (named barrier 1)
+template <int NW>
 __device__ __forceinline__ void consumer_sync() {
-  asm volatile("bar.sync 1, %0;" ::"n"(PK_WARPS * 32) : "memory");
+  asm volatile("bar.sync 1, %0;" ::"n"(NW * 32) : "memory");
 }
 // the same barrier, returning the OR of every consumer thread's v: all
 // consumers get the same answer, so they stop at the same chunk
+template <int NW>
 __device__ __forceinline__ bool consumer_sync_or(bool v) {
   uint32_t r;
   asm volatile(
       "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
       : "=r"(r)
-      : "r"((uint32_t)v), "n"(PK_WARPS * 32)
+      : "r"((uint32_t)v), "n"(NW * 32)
       : "memory");
   return r != 0;
 }
@@ -456,8 +459,8 @@ constexpr int SW_LPR_GLOBAL = 8;  // global slice: 8 also measured best (4 lanes
 // Warps 0..PK_WARPS-1 consume chunks; warp PK_WARPS produces them (one lane
 // issues the bulk copies).  full[s]: a chunk landed in stage s (transaction
 // count); empty[s]: the consumers finished with stage s.
-template <typename T, typename V, bool SMEMX, int SW_LPR>
-__global__ void __launch_bounds__((PK_WARPS + 1) * 32, 2)
+template <typename T, typename V, bool SMEMX, int SW_LPR, int NW = PK_WARPS>
+__global__ void __launch_bounds__((NW + 1) * 32, NW == PK_WARPS ? 2 : 4)
     k_schwarz_pk(PkArgs A, const T* __restrict__ r, T* __restrict__ z, T* xglob) {
   extern __shared__ __align__(128) unsigned char pk_smem[];
   __shared__ uint64_t full[NSTAGE], empty[NSTAGE], probe_bar;
@@ -465,7 +468,7 @@ __global__ void __launch_bounds__((PK_WARPS + 1) * 32, 2)
   int64_t issued = 0;  // chunks the producer lane has issued (used by its drain)
   const int j = A.natural ? (int)blockIdx.x : A.order[blockIdx.x], rhs = blockIdx.y;
   const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
-  const bool producer = wid == PK_WARPS;
+  const bool producer = wid == NW;
   r += (int64_t)rhs * A.nA;
   z += (int64_t)rhs * A.nA;
   unsigned char* ring = pk_smem;
@@ -512,11 +515,11 @@ __global__ void __launch_bounds__((PK_WARPS + 1) * 32, 2)
       }
     }
   } else {
-    for (int64_t q = tid; q < n; q += PK_WARPS * 32) {
+    for (int64_t q = tid; q < n; q += NW * 32) {
       const T v = r[A.snode[base + q]];
       xs[q] = (A.transpose && !A.owned[base + q]) ? (T)0 : v;
     }
-    consumer_sync();
+    consumer_sync<NW>();
     for (int64_t c = 0; c < nch; ++c) {
       const int st = (int)(c % NSTAGE);
       const bool probe = A.probe && c == 0;
@@ -541,7 +544,7 @@ __global__ void __launch_bounds__((PK_WARPS + 1) * 32, 2)
         const int e0 = ch.z ? 1 : 0, sub = lane & (LPR - 1);
         // rows rb + RPW * wid + lane / LPR; the loop is warp-uniform so that
         // every lane reaches the shuffles
-        for (int rb = 0; rb < ch.x; rb += RPW * PK_WARPS) {
+        for (int rb = 0; rb < ch.x; rb += RPW * NW) {
           const int rr = rb + RPW * wid + lane / LPR;
           const bool has = rr < ch.x;
           int4 h = make_int4(0, 0, 0, 0);
@@ -561,7 +564,7 @@ __global__ void __launch_bounds__((PK_WARPS + 1) * 32, 2)
       }
       // level barrier (the stage is free again) and one abort decision for
       // all consumers: the producer may set the flag at any time
-      const bool stop = consumer_sync_or(*(volatile int*)&abort_flag != 0);
+      const bool stop = consumer_sync_or<NW>(*(volatile int*)&abort_flag != 0);
       if (tid == 0) mbar_arrive(&empty[st]);
       if (stop) {
         abort_flag = 1;
@@ -674,6 +677,8 @@ static cpm_status allow_pk_smem(cudaStream_t) {
                         (const void*)k_schwarz_pk<T, V, false, 8>, (const void*)k_schwarz_pk<T, V, false, 16>};
   for (const void* f : fns)
     CPM_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PK_SMEM_MAX));
+  CPM_CUDA(cudaFuncSetAttribute((const void*)k_schwarz_pk<T, V, false, 8, PK_WARPS_FOUR>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PK_SMEM_MAX));
   done.fetch_or(bit);
   return CPM_OK;
 }
@@ -684,17 +689,20 @@ static cpm_status allow_pk_smem(cudaStream_t) {
 constexpr int PK_CARVE_ONE = 28;
 constexpr size_t PK_SMEM_ONE = 60 * 1024;
 
-template <typename T, typename V, bool SMEMX, int L>
+template <typename T, typename V, bool SMEMX, int L, int NW = PK_WARPS>
 static void launch_pk_l(int carve, dim3 g, size_t sm, cudaStream_t s, const PkArgs& A, const T* r, T* z, T* xl) {
-  constexpr int NT = (PK_WARPS + 1) * 32;
-  cudaFuncSetAttribute(k_schwarz_pk<T, V, SMEMX, L>, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
-  KL(k_schwarz_pk<T, V, SMEMX, L><<<g, NT, sm, s>>>(A, r, z, xl));
+  constexpr int NT = (NW + 1) * 32;
+  cudaFuncSetAttribute(k_schwarz_pk<T, V, SMEMX, L, NW>, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
+  KL(k_schwarz_pk<T, V, SMEMX, L, NW><<<g, NT, sm, s>>>(A, r, z, xl));
 }
 
+// ctas 4 (global slices only): four CTAs per SM of PK_WARPS_FOUR consumer
+// warps each, 8 lanes per row, so that up to 608 subdomains run at once
 template <typename T, typename V, bool SMEMX>
-static void launch_pk(int lanes, int carve, dim3 g, size_t sm, cudaStream_t s, const PkArgs& A, const T* r, T* z,
-                      T* xl) {
-  if (lanes == 4) launch_pk_l<T, V, SMEMX, 4>(carve, g, sm, s, A, r, z, xl);
+static void launch_pk(int lanes, int ctas, int carve, dim3 g, size_t sm, cudaStream_t s, const PkArgs& A, const T* r,
+                      T* z, T* xl) {
+  if (!SMEMX && ctas == 4) launch_pk_l<T, V, false, 8, PK_WARPS_FOUR>(carve, g, sm, s, A, r, z, xl);
+  else if (lanes == 4) launch_pk_l<T, V, SMEMX, 4>(carve, g, sm, s, A, r, z, xl);
   else if (lanes == 16) launch_pk_l<T, V, SMEMX, 16>(carve, g, sm, s, A, r, z, xl);
   else launch_pk_l<T, V, SMEMX, 8>(carve, g, sm, s, A, r, z, xl);
 }
@@ -726,9 +734,10 @@ static cpm_status run_pk(const oras_pc* P, const PackedFactors& pf, const T* r, 
   const bool smemx = P->xplace == 0 && ring + xsb <= 113 * 1024;
   // one CTA per SM with a small shared-memory carve-out (the rest of the SM's
   // memory is L1, which then holds most of one subdomain's global slice)
-  const bool one_cta = !smemx && P->l1 == 1 && ring <= PK_SMEM_ONE;
+  const bool one_cta = !smemx && P->ctas == 1 && ring <= PK_SMEM_ONE;
+  const bool four = !smemx && P->ctas == 4 && 4 * ring <= 220 * 1024;
   const size_t sm = smemx ? ring + xsb : (one_cta ? PK_SMEM_ONE : ring);
-  const int carve = one_cta ? PK_CARVE_ONE : (int)cudaSharedmemCarveoutDefault;
+  const int carve = one_cta ? PK_CARVE_ONE : (four ? (int)cudaSharedmemCarveoutMaxShared : (int)cudaSharedmemCarveoutDefault);
   if (sm > PK_SMEM_MAX) return fail(CPM_ERR_ARG, "Schwarz apply needs %zu bytes of shared memory", sm);
   CPM_TRY((allow_pk_smem<T, V>(s)));
   T* xloc = nullptr;
@@ -739,9 +748,10 @@ static cpm_status run_pk(const oras_pc* P, const PackedFactors& pf, const T* r, 
     T* xl = xloc ? xloc + (int64_t)r0 * P->nloc : nullptr;
     const int lanes = P->lanes ? P->lanes : (smemx ? SW_LPR_SMEM : SW_LPR_GLOBAL);
     if (smemx)
-      launch_pk<T, V, true>(lanes, carve, g, sm, s, A, r + (int64_t)r0 * P->nA, z + (int64_t)r0 * P->nA, xl);
+      launch_pk<T, V, true>(lanes, 0, carve, g, sm, s, A, r + (int64_t)r0 * P->nA, z + (int64_t)r0 * P->nA, xl);
     else
-      launch_pk<T, V, false>(lanes, carve, g, sm, s, A, r + (int64_t)r0 * P->nA, z + (int64_t)r0 * P->nA, xl);
+      launch_pk<T, V, false>(lanes, four ? 4 : 0, carve, g, sm, s, A, r + (int64_t)r0 * P->nA,
+                             z + (int64_t)r0 * P->nA, xl);
     if (transpose) {
       dim3 g2(grid_for(P->nA, 256), nr);
       KL(k_gather_T2<T><<<g2, 256, 0, s>>>(P->nA, P->nloc, P->mcnt, P->mloc, xl, z + (int64_t)r0 * P->nA));
@@ -778,7 +788,7 @@ cpm_status oras_tune(oras_pc* P, cpm_dtype dt, int reps, cudaStream_t s, oras_tu
   if (cudaMemsetAsync(r, 0, P->nA * esz, s) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
       cudaEventCreate(&e1) != cudaSuccess)
     return done(fail(CPM_ERR_CUDA, "autotune set-up failed"));
-  oras_tuning keep{P->xplace, P->lanes, P->schedule, P->l1, 0, P->wait_polls}, win = keep;
+  oras_tuning keep{P->xplace, P->lanes, P->schedule, P->ctas, 0, P->wait_polls}, win = keep;
   double win_ms = 1e300;
   const int lanes[3] = {4, 8, 16};
   if ((st = oras_run(P, r, z, dt, 1, 0, s)) != CPM_OK) return done(st);  // packs this precision if needed
@@ -787,12 +797,14 @@ cpm_status oras_tune(oras_pc* P, cpm_dtype dt, int reps, cudaStream_t s, oras_tu
   for (int xp = 0; xp < 2; ++xp)
     for (int li = 0; li < 3; ++li)
       for (int sc = 0; sc < 2; ++sc)
-        for (int l1 = 0; l1 < 2; ++l1) {
-        if (l1 == 1 && xp == 0 && fits) continue;  // l1 only matters for global slices
+        for (int ci = 0; ci < 3; ++ci) {
+        const int ctas = ci == 0 ? 0 : (ci == 1 ? 1 : 4);
+        if (ctas != 0 && xp == 0 && fits) continue;  // CTAs per SM only vary for global slices
+        if (ctas == 4 && lanes[li] != 8) continue;    // the four-CTA kernel uses 8 lanes per row
         P->xplace = xp;
         P->lanes = lanes[li];
         P->schedule = sc;
-        P->l1 = l1;
+        P->ctas = ctas;
         if ((st = oras_run(P, r, z, dt, 1, 0, s)) != CPM_OK) return done(st);  // warm-up (packs on first use)
         cudaEventRecord(e0, s);
         for (int q = 0; q < reps; ++q)
@@ -803,20 +815,20 @@ cpm_status oras_tune(oras_pc* P, cpm_dtype dt, int reps, cudaStream_t s, oras_tu
         cudaEventElapsedTime(&ms, e0, e1);
         if (ms / reps < win_ms) {
           win_ms = ms / reps;
-          win = oras_tuning{xp, lanes[li], sc, l1, 0, keep.wait_polls};
+          win = oras_tuning{xp, lanes[li], sc, ctas, 0, keep.wait_polls};
         }
       }
   if ((st = oras_take_error(P, s)) != CPM_OK) {
     P->xplace = keep.xplace;
     P->lanes = keep.lanes;
     P->schedule = keep.schedule;
-    P->l1 = keep.l1;
+    P->ctas = keep.ctas;
     return done(st);
   }
   P->xplace = win.xplace;
   P->lanes = win.lanes;
   P->schedule = win.schedule;
-  P->l1 = win.l1;
+  P->ctas = win.ctas;
   if (best) *best = win;
   if (best_ms) *best_ms = win_ms;
   return done(CPM_OK);

@@ -13,7 +13,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 STRUCTS = {
     "cpm_surface": ["kind", "param"],
     "oras_params": ["nparts", "overlap", "robin", "alpha", "alpha_cross", "store", "order", "coarse"],
-    "oras_tuning": ["xplace", "lanes", "schedule", "l1", "probe_timeout", "wait_polls"],
+    "oras_tuning": ["xplace", "lanes", "schedule", "ctas", "probe_timeout", "wait_polls"],
     "cpm_solve_params": ["restart", "maxit", "rtol", "mixed", "reorth", "inner_rtol", "timing"],
     "cpm_solve_info": ["iters", "restarts", "ir_steps", "rel_residual", "status", "ms_precond", "ms_operator",
                        "n_precond", "n_operator"],
