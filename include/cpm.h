@@ -199,11 +199,11 @@ cpm_status oras_apply(const oras_pc* pc, const void* r, void* z, cpm_dtype dtype
  *                  slice)
  *   schedule       order in which subdomains are handed to CTAs: 0 longest
  *                  first (default), 1 partition order
- *   ctas           CTAs per SM when the local vectors live in global slices: 0
- *                  two (default); 1 one, with a 64 KB shared-memory carve-out that
- *                  leaves the rest of the SM's 256 KB to the L1 cache holding the
- *                  slice; 4 four, of 6 consumer warps each (8 lanes per row), so
- *                  that up to 608 subdomains run at once
+ *   ctas           CTAs per SM when the local vectors live in global slices: 1
+ *                  one, with a 64 KB shared-memory carve-out that leaves the rest
+ *                  of the SM's 256 KB to the L1 cache holding the slice (0: the
+ *                  default, this one); 2 two; 4 four, of 6 consumer warps each
+ *                  (8 lanes per row), so that up to 608 subdomains run at once
  *   probe_timeout  0 normal; 1 failure-path test: the first factor-chunk wait
  *                  of every subdomain waits on a barrier that nothing completes,
  *                  so each CTA runs out after wait_polls polls, waits for its
@@ -226,7 +226,7 @@ cpm_status oras_get_tuning(const oras_pc* pc, oras_tuning* t);
 
 /* oras_autotune -- time every combination of xplace (both when the local
  * vectors fit in shared memory), lanes (4, 8, 16), schedule (0, 1) and ctas
- * (0, 1, 4; where the local vectors live in global slices) on
+ * (1, 2, 4; where the local vectors live in global slices) on
  * `reps` forward applies of dtype (CPM_F32 or CPM_F64) each, with CUDA events
  * on `stream`, and keep the fastest as the preconditioner's setting (the
  * probe stays off).  best (HOST, may be NULL) receives it and best_ms (HOST,
@@ -306,6 +306,10 @@ cpm_status cpm_solve_adjoint(const cpm_band* band, const oras_pc* pc, double c, 
  * until the others finish their cycle; each cycle ends with every system's
  * true FP64 residual.  mixed = 1 runs the operator and preconditioner in FP32
  * inside FP64 iterative refinement (FP32 or BF16 factors required).
+ * The lockstep solver keeps (restart + 7) doubles per unknown of every system
+ * it runs at once, so the problems are cut, in order, into consecutive
+ * groups whose storage fits min(32 GB, 40 % of the device's free memory),
+ * solved one group after another within the call.
  * Returns CPM_ERR_NOT_CONVERGED if any system missed rtol within maxit
  * iterations (its info[] entry says which).  Synchronises the stream.
  * The paper solves one problem per PETSc run; batching is this library's. */

@@ -521,7 +521,9 @@ cpm_status run_cycle(Batch& Bt, double* x, bool f32, int transpose, int maxit, d
 
 }  // namespace
 
-cpm_status solve_batch(int nprob, const cpm_band* const* bands, const oras_pc* const* pcs, const double* c,
+namespace {
+// one group of problems solved in lockstep
+cpm_status solve_group(int nprob, const cpm_band* const* bands, const oras_pc* const* pcs, const double* c,
                        const int32_t* nrhs, const double* f, double* u, const cpm_solve_params* prm,
                        cpm_solve_info* info, int transpose, cudaStream_t s) {
   Batch Bt;
@@ -680,6 +682,43 @@ cpm_status solve_batch(int nprob, const cpm_band* const* bands, const oras_pc* c
 #undef BTRY
   Bt.release(s);
   cudaStreamSynchronize(s);
+  return all;
+}
+}  // namespace
+
+// Memory-bounded batching: the lockstep solver holds its Krylov basis and
+// work vectors for every system at once ((restart + 7) doubles per unknown),
+// so the problems are cut, in order, into consecutive groups whose storage
+// fits min(32 GB, 40 % of the device's free memory) and the groups are
+// solved one after another.
+cpm_status solve_batch(int nprob, const cpm_band* const* bands, const oras_pc* const* pcs, const double* c,
+                       const int32_t* nrhs, const double* f, double* u, const cpm_solve_params* prm,
+                       cpm_solve_info* info, int transpose, cudaStream_t s) {
+  size_t freeb = 0, totalb = 0;
+  CPM_CUDA(cudaMemGetInfo(&freeb, &totalb));
+  const double budget = std::min(32e9, 0.4 * (double)freeb);
+  const double per_unknown = 8.0 * (prm->restart + 7);
+  cpm_status all = CPM_OK;
+  int p0 = 0;
+  int64_t off = 0, sys0 = 0;
+  while (p0 < nprob) {
+    int p1 = p0;
+    double bytes = 0;
+    int64_t len = 0, nsys = 0;
+    do {
+      bytes += per_unknown * (double)nrhs[p1] * (double)bands[p1]->nA;
+      len += (int64_t)nrhs[p1] * bands[p1]->nA;
+      nsys += nrhs[p1];
+      ++p1;
+    } while (p1 < nprob && bytes + per_unknown * (double)nrhs[p1] * (double)bands[p1]->nA <= budget);
+    const cpm_status st = solve_group(p1 - p0, bands + p0, pcs ? pcs + p0 : nullptr, c + p0, nrhs + p0, f + off,
+                                      u + off, prm, info + sys0, transpose, s);
+    if (st == CPM_ERR_NOT_CONVERGED) all = CPM_ERR_NOT_CONVERGED;
+    else if (st != CPM_OK) return st;
+    off += len;
+    sys0 += nsys;
+    p0 = p1;
+  }
   return all;
 }
 

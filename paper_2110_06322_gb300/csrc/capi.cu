@@ -144,7 +144,8 @@ cpm_status oras_set_tuning(oras_pc* pc, const oras_tuning* t) {
   if (t->lanes != 0 && t->lanes != 4 && t->lanes != 8 && t->lanes != 16)
     return fail(CPM_ERR_ARG, "lanes must be 0, 4, 8 or 16");
   if (t->schedule != 0 && t->schedule != 1) return fail(CPM_ERR_ARG, "schedule must be 0 or 1");
-  if (t->ctas != 0 && t->ctas != 1 && t->ctas != 4) return fail(CPM_ERR_ARG, "ctas must be 0, 1 or 4");
+  if (t->ctas != 0 && t->ctas != 1 && t->ctas != 2 && t->ctas != 4)
+    return fail(CPM_ERR_ARG, "ctas must be 0, 1, 2 or 4");
   if (t->probe_timeout != 0 && t->probe_timeout != 1) return fail(CPM_ERR_ARG, "probe_timeout must be 0 or 1");
   if (t->wait_polls < 0 || t->wait_polls > 0xffffffffll) return fail(CPM_ERR_ARG, "wait_polls must be in [0, 2^32)");
   pc->xplace = t->xplace;

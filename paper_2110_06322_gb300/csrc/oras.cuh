@@ -77,7 +77,7 @@ struct oras_pc {
   int xplace = 0;             // 0 local vector in shared memory when it fits, 1 always a global slice
   int lanes = 0;              // lanes per factor row in the sweeps (0: by placement)
   int schedule = 0;           // 0 subdomains longest first, 1 in partition order
-  int ctas = 0;               // global-slice path: 0 two CTAs per SM, 1 one (larger L1), 4 four (6 consumer warps)
+  int ctas = 0;               // global-slice path: CTAs per SM, 1 (larger L1), 2 or 4 (6 consumer warps); 0 = 1
   int probe_timeout = 0;      // failure-path test: the first chunk wait can only run out
   int64_t wait_polls = 0;     // polls of each consumer-side wait (0: the default)
   // two-level variant (coarse correction on one constant per disjoint part)
