@@ -4,12 +4,12 @@
 #include "common.cuh"
 
 // One chunk of level-packed factor rows (see packed.cu): byte offset and size
-// in the packed stream, its rows and entries, and whether its rows are scaled
-// by a stored reciprocal diagonal.
+// in the packed stream, its rows and entries, whether its rows are scaled by a
+// stored reciprocal diagonal, and whether it is the last chunk of its level.
 struct ChunkRec {
   int64_t off;
   int32_t bytes, nrows, ne, div;
-  int32_t pad[2];
+  int32_t lend, pad;
 };
 
 struct PackedFactors {

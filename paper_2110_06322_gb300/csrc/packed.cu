@@ -20,8 +20,8 @@
 // cp.async.bulk (the 1-D TMA copy) and mbarrier transaction counts, NSTAGE-1
 // chunks ahead; all warps consume the current chunk from shared memory
 // (SW_LPR lanes per row: gather the local vector, multiply, shuffle-reduce;
-// 32 / SW_LPR rows share each shuffle) and meet at
-// one CTA barrier per chunk, which is also the level barrier.  The local
+// 32 / SW_LPR rows share each shuffle), release each stage warp by warp and
+// meet at one barrier per level (at the level's last chunk).  The local
 // vector lives in shared memory when it fits, else in a global slice.  Every
 // mbarrier wait is bounded.  A wait that runs out sets an error flag; the
 // producer then stops issuing, and before the CTA returns it waits (bounded)
@@ -100,6 +100,7 @@ __global__ void k_pack_plan(int32_t nl, int np, SweepSrc S, int vsize, int mode,
           rec[c].nrows = (int32_t)nrows;
           rec[c].ne = (int32_t)ne;
           rec[c].div = kindflag;
+          rec[c].lend = 0;  // more chunks of this level follow
         }
         ++c;
         ++cnt;
@@ -120,6 +121,7 @@ __global__ void k_pack_plan(int32_t nl, int np, SweepSrc S, int vsize, int mode,
         rec[c].nrows = (int32_t)nrows;
         rec[c].ne = (int32_t)ne;
         rec[c].div = kindflag;
+        rec[c].lend = 1;  // the level's last chunk
       }
       ++cnt;
     }
@@ -231,7 +233,9 @@ __global__ void k_chunk_place(int64_t n, const ChunkRec* __restrict__ plan, cons
     R.off = off[c];
     R.bytes = (int32_t)sz[c];
     rec[c] = R;
-    csz[c] = (uint16_t)(sz[c] >> 4);
+    // size in 16-byte units (at most CHUNK_BYTES / 16 = 1536), top bit: the
+    // chunk ends its level
+    csz[c] = (uint16_t)((sz[c] >> 4) | (plan[c].lend ? 0x8000 : 0));
   }
 }
 
@@ -482,7 +486,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, NW == PK_WARPS ? 2 : 4)
     abort_flag = 0;
     for (int q = 0; q < NSTAGE; ++q) {
       mbar_init(&full[q], 1);
-      mbar_init(&empty[q], 1);
+      mbar_init(&empty[q], NW);  // one arrival per consumer warp
     }
     mbar_init(&probe_bar, 1);  // never arrived on: a wait on it can only run out
     fence_mbar_init();
@@ -506,7 +510,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, NW == PK_WARPS ? 2 : 4)
             break;
           }
         }
-        const uint32_t bytes = (uint32_t)csz[c] << 4;
+        const uint32_t bytes = (uint32_t)(csz[c] & 0x7fff) << 4;
         fence_proxy_async();
         mbar_expect_tx(&full[st], bytes);
         bulk_g2s(ring + st * CHUNK_BYTES, A.data + off, bytes, &full[st]);
@@ -562,13 +566,21 @@ __global__ void __launch_bounds__((NW + 1) * 32, NW == PK_WARPS ? 2 : 4)
           }
         }
       }
-      // level barrier (the stage is free again) and one abort decision for
-      // all consumers: the producer may set the flag at any time
-      const bool stop = consumer_sync_or<NW>(*(volatile int*)&abort_flag != 0);
-      if (tid == 0) mbar_arrive(&empty[st]);
-      if (stop) {
-        abort_flag = 1;
-        break;
+      // this warp is done reading the stage
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[st]);
+      // Rows of one level are independent, so the consumers meet only at the
+      // last chunk of a level (the next level reads its results), and take one
+      // abort decision there for all of them: the producer may set the flag at
+      // any time.  The level ends come from the chunk-size table that every
+      // thread copied before the loop, so all warps meet at the same chunks
+      // even when a wait ran out.
+      if (csz[c] >> 15) {
+        const bool stop = consumer_sync_or<NW>(*(volatile int*)&abort_flag != 0);
+        if (stop) {
+          abort_flag = 1;
+          break;
+        }
       }
     }
   }
