@@ -609,7 +609,7 @@ __global__ void __launch_bounds__(32)
     k_levels_smem(const int64_t* __restrict__ sptr, const int64_t* __restrict__ rptr,
                   const int32_t* __restrict__ col, const int32_t* __restrict__ dpos, int lower, int32_t* lev,
                   int32_t* nlev) {
-  extern __shared__ int16_t slev[];
+  extern __shared__ uint16_t slev[];  // levels <= rows <= 65535 (16-bit local columns)
   const int lane = threadIdx.x;
   const int j = blockIdx.x;
   const int64_t base = sptr[j], n = sptr[j + 1] - base;
@@ -642,7 +642,7 @@ __global__ void __launch_bounds__(32)
     for (int o = 16; o > 0; o >>= 1) l = max(l, __shfl_xor_sync(FULL, l, o));
     const int64_t tl = lower ? t : n - 1 - t;
     if (lane == 0) {
-      slev[tl] = (int16_t)(l + 1);
+      slev[tl] = (uint16_t)(l + 1);
       lev[base + tl] = l + 1;
     }
     mx = max(mx, l + 1);
@@ -841,8 +841,8 @@ cpm_status build_schedule(oras_pc* P, const int64_t* rptr, const int32_t* col, c
   int32_t *lev = nullptr, *nlev = nullptr;
   CPM_TRY(dalloc(&lev, nloc, s));
   CPM_TRY(dalloc(&nlev, np, s));
-  if (P->max_rows < 32768 && P->max_rows * (int64_t)sizeof(int16_t) <= 200 * 1024) {
-    const int sm = (int)std::max<int64_t>(P->max_rows * (int64_t)sizeof(int16_t), 16);
+  if (P->max_rows <= 65535 && P->max_rows * (int64_t)sizeof(uint16_t) <= 200 * 1024) {
+    const int sm = (int)std::max<int64_t>(P->max_rows * (int64_t)sizeof(uint16_t), 16);
     CPM_CUDA(cudaFuncSetAttribute(k_levels_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
     KL(k_levels_smem<<<np, 32, sm, s>>>(P->sptr, rptr, col, dpos, lower, lev, nlev));
   } else {
