@@ -195,72 +195,6 @@ __global__ void __launch_bounds__(EGROUP_WIN)
   }
 }
 
-// The same pass for p = 3 with each work item on a pair of lanes: lane 2k
-// holds the cube's slabs u = 0, 1 and lane 2k + 1 the slabs u = 2, 3 (32
-// values each instead of 64), so twice as many warps fit on an SM to hide the
-// gathers' latency.  Both lanes evaluate every row of the item on their half
-// of the cube; one shuffle adds the halves (first half + second half, the
-// same sum on both lanes) and the two lanes store the value pair's two words.
-__global__ void __launch_bounds__(EGROUP_WIN)
-    k_erow_grp_pair(ApplyGeom G, int64_t nitem, const int2* __restrict__ items, const float4* __restrict__ grec,
-                    const float* __restrict__ x, float* __restrict__ w) {
-  constexpr int P = 3;
-  const int rhs = blockIdx.y;
-  x += (int64_t)rhs * G.nA;
-  w += (int64_t)rhs * G.nR * 2;
-  const int lane = threadIdx.x & 31, half = lane & 1;
-  const unsigned pm = 3u << (lane & 30);  // this lane and its partner
-  for (int64_t it = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 1; it < nitem;
-       it += ((int64_t)gridDim.x * blockDim.x) >> 1) {
-    const int2 I = items[it];
-    const int start = I.x >> 4, rows = (I.x & 15) + 1;
-    const int b0 = G.ijkA[3 * I.y] + 2 * half, b1 = G.ijkA[3 * I.y + 1], b2 = G.ijkA[3 * I.y + 2];
-    float X[2][P + 1][P + 1];
-#pragma unroll
-    for (int u = 0; u < 2; ++u)
-#pragma unroll
-      for (int v = 0; v <= P; ++v) {
-        const float* xp = x + bm_rank_known(G.amap, G.g, b0 + u, b1 + v, b2);
-#pragma unroll
-        for (int t = 0; t <= P; ++t) X[u][v][t] = __ldg(xp + t);
-      }
-    // reference node (1, 1, 1) of the cube: slab u = 1, held by the first lane
-    const float xref = __shfl_sync(pm, X[1][1][1], lane & 30);
-#pragma unroll
-    for (int u = 0; u < 2; ++u)
-#pragma unroll
-      for (int v = 0; v <= P; ++v)
-#pragma unroll
-        for (int t = 0; t <= P; ++t) X[u][v][t] -= xref;
-    float4 nxt = __ldg(grec + start);
-    for (int k = 0; k < rows; ++k) {
-      const float4 cur = nxt;
-      if (k + 1 < rows) nxt = __ldg(grec + start + k + 1);
-      const int32_t r = __float_as_int(cur.w);
-      float l[3][P + 1];
-      lagrange_f32<P>(cur.x, l[0]);
-      lagrange_f32<P>(cur.y, l[1]);
-      lagrange_f32<P>(cur.z, l[2]);
-      const float lu[2] = {half ? l[0][2] : l[0][0], half ? l[0][3] : l[0][1]};
-      float acc = 0;
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        float au = 0;
-#pragma unroll
-        for (int v = 0; v <= P; ++v) {
-          float av = 0;
-#pragma unroll
-          for (int t = 0; t <= P; ++t) av += l[2][t] * X[u][v][t];
-          au += l[1][v] * av;
-        }
-        acc += lu[u] * au;
-      }
-      const float other = __shfl_xor_sync(pm, acc, 1);
-      w[2 * r + half] = half ? xref : acc + other;
-    }
-  }
-}
-
 // ---- grouping of the E rows by cube (set-up, at band build)
 // key of row r: canonical rank of its cube base (a node of Sigma_A: the
 // cube lies inside Sigma_A); count rows per key
@@ -530,10 +464,7 @@ cpm_status erow_pass(const cpm_band* B, const ApplyGeom& G, const T* x, T* w, in
     dim3 g1(grid_for(B->nitem, EGROUP_WIN), nr);
     const int2* it = reinterpret_cast<const int2*>(B->gitem);
     const float4* rec = reinterpret_cast<const float4*>(B->grec);
-    if (B->p == 3) {
-      dim3 gp(grid_for(2 * B->nitem, EGROUP_WIN), nr);
-      KL(k_erow_grp_pair<<<gp, EGROUP_WIN, 0, s>>>(G, B->nitem, it, rec, x, w));
-    }
+    if (B->p == 3) KL(k_erow_grp<3><<<g1, EGROUP_WIN, 0, s>>>(G, B->nitem, it, rec, x, w));
     else KL(k_erow_grp<2><<<g1, EGROUP_WIN, 0, s>>>(G, B->nitem, it, rec, x, w));
   } else {
     dim3 g1(grid_for(B->nR, 256), nr);
