@@ -66,10 +66,10 @@ REF_RTOL = 1e-10   # FP64 reference solution: 100x below the 1e-8 error statemen
 E2E_STEPS = 3      # end-to-end steps (host buffers): at most this many
 # DRAM bytes (read + write) per stored factor entry of one FP32 Schwarz apply at the headline size,
 # from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, one pass) of the full h = 0.002 /
-# 512-part launch with the default settings (8 lanes per row, local vectors in global slices, two CTAs
-# per SM): 21,919,661,824 + 593,259,520 bytes over 3,232,543,691 entries.  Re-measure when the kernel
-# or its default settings change.
-SCHWARZ_DRAM_PER_ENTRY = (21919661824 + 593259520) / 3232543691
+# 512-part launch with the default settings (8 lanes per row, local vectors in global slices, one CTA
+# per SM, consumers meeting at level ends): 21,017,388,288 + 541,374,464 bytes over 3,232,543,691
+# entries.  Re-measure when the kernel or its default settings change.
+SCHWARZ_DRAM_PER_ENTRY = (21017388288 + 541374464) / 3232543691
 
 
 def parse(argv=None):
@@ -465,6 +465,12 @@ def extras(torch, cpm, args, w, f, step, n, rtol):
     out["reference"] = {"rtol": REF_RTOL, "extra_iters": iref["iters"], "extra_s": tref, "status": iref["status"],
                         "rel_residual": iref["rel_residual"], "what": "GPU FP64 solve continued from the FP64 "
                         "solution to the reference tolerance (FP64 solves are parity-tested against the oracle)"}
+    # the apply autotuner on this preconditioner, then a mixed solve with its pick
+    (tuned, tuned_ms), t_tune = _timed(torch, lambda: P.autotune(cpm.CPM_F32, reps=3))
+    (u32t, i32t), t32t = _timed(torch, lambda: cpm.solve(B, f, P, rtol=rtol, restart=w["restart"], maxit=100000,
+                                                         mixed=True, reorth=0))
+    out["autotuned"] = {"setting": tuned, "apply_ms": tuned_ms, "autotune_s": t_tune, "solve_s": t32t,
+                        "iters": i32t["iters"], "err_vs_reference": _rel(torch, u32t, uref)}
     del P
     # BF16 factor storage (ablation)
     (PB, tb_set) = _timed(torch, lambda: schwarz_for(cpm, B, w, cpm.CPM_BF16))
@@ -493,6 +499,10 @@ def extras(torch, cpm, args, w, f, step, n, rtol):
 
 
 # ---------------------------------------------------------------- other workloads
+def _progress(msg):
+    print(msg, file=sys.stderr, flush=True)
+
+
 def draw_problems(nprob, hs, seed):
     """Batched workload: spheres of radius U[0.5, 1.5] and tori R ~ U[0.8,
     1.2], r ~ U[0.2, 0.5] in turn, spacing drawn from hs, c log-uniform in
@@ -544,36 +554,49 @@ def run_batch(args):
         F = np.stack([inputs.gaussian_vector(sp["seed"] + r, B.n_active) for r in range(sp["nrhs"])])
         probs.append((B, P, sp["c"]))
         rhs.append(torch.from_numpy(F).cuda())
+        if len(probs) % 16 == 0:
+            _progress(f"batch: {len(probs)} problems set up, {time.perf_counter() - t0:.1f} s")
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t0
+    _progress(f"batch: set-up of {len(probs)} problems {t_setup:.1f} s")
     opts = dict(rtol=1e-8, maxit=100000, mixed=True)
     cpm.solve_batch(probs[:2], rhs[:2], **opts)
     L0 = cpm.cpm_kernel_launches()
     (res, t_batch) = _timed(torch, lambda: cpm.solve_batch(probs, rhs, **opts))
     launches = cpm.cpm_kernel_launches() - L0
     U, infos = res
+    _progress(f"batch: {len(infos)} systems in one call {t_batch:.1f} s")
     pt_iters, q = 0, 0
     for (b, _, _), f in zip(probs, rhs):
         for _ in range(f.shape[0]):
             pt_iters += int(b.n_active) * infos[q]["iters"]
             q += 1
+    # like-for-like comparison on every 4th problem: one batched call against
+    # the same systems solved one by one
+    sub = list(range(0, len(probs), 4))
+    (_, t_bsub) = _timed(torch, lambda: cpm.solve_batch([probs[k] for k in sub], [rhs[k] for k in sub], **opts))
 
     def singles():
-        for (B, P, c), f in zip(probs, rhs):
-            for r in range(f.shape[0]):
-                cpm.solve(B, f[r].contiguous(), P, c=c, **opts)
+        for k in sub:
+            B, P, c = probs[k]
+            for r in range(rhs[k].shape[0]):
+                cpm.solve(B, rhs[k][r].contiguous(), P, c=c, **opts)
     (_, t_single) = _timed(torch, singles)
+    _progress(f"batch: subset of {len(sub)} problems batched {t_bsub:.1f} s, one by one {t_single:.1f} s")
     n_sys = len(infos)
     line = {"metric": "batched ORAS-GMRES solves/s (uneven problems, one call)", "value": n_sys / t_batch,
             "unit": "solves/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": f"batch: {len(probs)} problems / {n_sys} systems, spacings {hs}, "
+            "config": {"workload": f"batch: {len(probs)} problems / {n_sys} systems / "
+                                   f"{sum(int(b.n_active) * f.shape[0] for (b, _, _), f in zip(probs, rhs))} "
+                                   f"unknowns, spacings {hs}, "
                                    f"{min(int(b.n_active) for b, _, _ in probs)}-"
                                    f"{max(int(b.n_active) for b, _, _ in probs)} band points, c log-uniform "
                                    "0.1-1000, 1-8 right-hand sides, two-level Schwarz (autotuned apply), "
                                    "mixed FP32/FP64 to 1e-8, CUDA-graph cycles"},
-            "setup_s": t_setup, "batch_s": t_batch, "single_s": t_single, "batch_speedup": t_single / t_batch,
-            "band_pt_iters_per_s": pt_iters / t_batch, "iters_max": max(i["iters"] for i in infos),
-            "iters_total": sum(i["iters"] for i in infos),
+            "setup_s": t_setup, "batch_s": t_batch, "band_pt_iters_per_s": pt_iters / t_batch,
+            "subset": {"problems": len(sub), "systems": sum(int(rhs[k].shape[0]) for k in sub),
+                       "batch_s": t_bsub, "single_s": t_single, "batch_speedup": t_single / t_bsub},
+            "iters_max": max(i["iters"] for i in infos), "iters_total": sum(i["iters"] for i in infos),
             "converged": sum(1 for i in infos if i["status"] == 0),
             "worst_rel_residual": max(i["rel_residual"] for i in infos), "gpu_launches": launches}
     print(json.dumps(line), flush=True)

@@ -193,10 +193,23 @@ cpm_status oras_apply(const oras_pc* pc, const void* r, void* z, cpm_dtype dtype
  * counterpart (its subdomain solves are PETSc calls, Section 4.1.1).
  *   xplace         where each subdomain's local vector lives during the
  *                  triangular sweeps: 0 in shared memory when it fits beside the
- *                  factor ring (default), 1 always in a global-memory slice
+ *                  factor ring (default), else in a global-memory slice; 1
+ *                  always in a global-memory slice; 2 (FP32 applies) as 0, but
+ *                  where the FP32 local vector does not fit it is held in FP16
+ *                  in shared memory (one CTA per SM, 8 lanes per row, 12
+ *                  consumer warps) when that fits: the entries of R_j r are
+ *                  scaled by a power of two per subdomain so the largest is
+ *                  below 2^10, and rows that carry a reciprocal pivot are
+ *                  computed as (x_i sigma - sum) / pivot with a power of two
+ *                  sigma near the pivot, so stored values stay in FP16's normal
+ *                  range; arithmetic stays FP32.  This changes the
+ *                  preconditioner's rounding (about 1e-3 relative), not the
+ *                  method; the FP32 inner cycles of the mixed solver are
+ *                  flexible, so they use exactly the preconditioned vectors
+ *                  they computed.  3 as 2 with 24 consumer warps.  FP64
+ *                  applies treat 2 and 3 as 0.  The autotuner tries 0 and 1 only.
  *   lanes          lanes of a warp per factor row in the sweeps: 4, 8 or 16
- *                  (0: 8 with the local vector in shared memory, 4 in a global
- *                  slice)
+ *                  (0: 8)
  *   schedule       order in which subdomains are handed to CTAs: 0 longest
  *                  first (default), 1 partition order
  *   ctas           CTAs per SM when the local vectors live in global slices: 1

@@ -380,7 +380,9 @@ class Schwarz:
 
     def set_tuning(self, xplace=0, lanes=0, schedule=0, probe_timeout=0, wait_polls=0, ctas=0):
         """Run-time settings of the apply (oras_set_tuning): local-vector
-        placement, lanes per factor row, subdomain schedule, CTAs per SM
+        placement (0 shared memory when it fits, 1 global slice, 2 and 3 an
+        FP16 local vector in shared memory for FP32 applies whose FP32 one
+        does not fit), lanes per factor row, subdomain schedule, CTAs per SM
         for global slices, the failure-path probe and the wait bound."""
         oras_set_tuning(self.handle, xplace, lanes, schedule, probe_timeout, wait_polls, ctas)
 

@@ -140,7 +140,7 @@ cpm_status oras_apply(const oras_pc* pc, const void* r, void* z, cpm_dtype dtype
 
 cpm_status oras_set_tuning(oras_pc* pc, const oras_tuning* t) {
   if (!pc || !t) return fail(CPM_ERR_ARG, "null argument");
-  if (t->xplace != 0 && t->xplace != 1) return fail(CPM_ERR_ARG, "xplace must be 0 or 1");
+  if (t->xplace < 0 || t->xplace > 3) return fail(CPM_ERR_ARG, "xplace must be 0, 1, 2 or 3");
   if (t->lanes != 0 && t->lanes != 4 && t->lanes != 8 && t->lanes != 16)
     return fail(CPM_ERR_ARG, "lanes must be 0, 4, 8 or 16");
   if (t->schedule != 0 && t->schedule != 1) return fail(CPM_ERR_ARG, "schedule must be 0 or 1");

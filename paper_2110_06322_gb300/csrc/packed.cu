@@ -397,7 +397,33 @@ __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier
 template <typename V, typename T>
 __device__ __forceinline__ T cvt(V v) {
   if constexpr (std::is_same<V, __nv_bfloat16>::value) return (T)__bfloat162float(v);
+  else if constexpr (std::is_same<V, __half>::value) return (T)__half2float(v);
   else return (T)v;
+}
+// store a sweep value in the local vector's type (FP16: round to nearest)
+template <typename X, typename T>
+__device__ __forceinline__ X to_x(T v) {
+  if constexpr (std::is_same<X, __half>::value) return __float2half_rn((float)v);
+  else return (X)v;
+}
+
+// FP16 local vector: the entries of R_j r are scaled by a power of two that
+// puts the largest one in [2^(XS_EXP-1), 2^XS_EXP), which leaves a factor
+// 2^(15 - XS_EXP) of FP16's range (largest finite 65504) for growth in the
+// sweeps and keeps entries down to 2^-24 of the largest one representable.
+constexpr int XS_EXP = 10;
+__device__ __forceinline__ float pow2_scale(float amax) {
+  const int be = (__float_as_int(amax) >> 23) & 0xff;  // biased exponent: amax in [2^(be-127), 2^(be-126))
+  if (!(amax > 0.f) || be == 0xff) return 1.f;
+  const int k = max(-120, min(120, XS_EXP + 126 - be));
+  return __int_as_float((127 + k) << 23);
+}
+// the power of two sigma with sigma * d in [1, 2) for a nonzero finite d
+// (d: the reciprocal pivot of a backward row); 1 otherwise
+__device__ __forceinline__ float pow2_recip(float d) {
+  const int be = (__float_as_int(fabsf(d)) >> 23) & 0xff;
+  if (be == 0 || be >= 254) return 1.f;
+  return __int_as_float((254 - be) << 23);
 }
 
 struct PkArgs {
@@ -445,12 +471,12 @@ __device__ __forceinline__ bool consumer_sync_or(bool v) {
 // vector are in flight at once: a few for a local vector in shared memory
 // (short latency), enough to cover a whole row when it lives in a global
 // slice (one L2 round trip per row instead of several).
-template <typename T, typename V, int LPR, int UNR>
+template <typename T, typename V, int LPR, int UNR, typename X>
 __device__ __forceinline__ T row_dot(const int4 h, int e0, int sub, const V* vals, const uint16_t* cols,
-                                     const T* xs) {
+                                     const X* xs) {
   T s = 0;
 #pragma unroll UNR
-  for (int e = e0 + sub; e < h.z; e += LPR) s += cvt<V, T>(vals[h.y + e]) * xs[cols[h.y + e]];
+  for (int e = e0 + sub; e < h.z; e += LPR) s += cvt<V, T>(vals[h.y + e]) * cvt<X, T>(xs[cols[h.y + e]]);
   return s;
 }
 
@@ -463,12 +489,29 @@ constexpr int SW_LPR_GLOBAL = 8;  // global slice: 8 also measured best (4 lanes
 // Warps 0..PK_WARPS-1 consume chunks; warp PK_WARPS produces them (one lane
 // issues the bulk copies).  full[s]: a chunk landed in stage s (transaction
 // count); empty[s]: the consumers finished with stage s.
-template <typename T, typename V, bool SMEMX, int SW_LPR, int NW = PK_WARPS>
-__global__ void __launch_bounds__((NW + 1) * 32, NW == PK_WARPS ? 2 : 4)
+//
+// XT is the type of the local vector: T, or FP16 (in shared memory only, for
+// FP32 applies whose subdomains do not fit there in FP32).  With FP16 the
+// entries of R_j r are scaled by alpha (pow2_scale) and the rows that carry a
+// reciprocal pivot d compute (x_i * sigma - sum) * d, with sigma = pow2_recip
+// of the first such row's d, so that their results (x_i / pivot ~ 1e-6 x_i on
+// the benchmark grids) stay in FP16's normal range; the output is unscaled by
+// 1 / (alpha * sigma), both powers of two.
+template <int NW, typename XT>
+constexpr int pk_min_blocks() {
+  return NW == PK_WARPS_FOUR ? 4 : (std::is_same<XT, __half>::value ? 1 : 2);
+}
+
+template <typename T, typename V, bool SMEMX, int SW_LPR, int NW = PK_WARPS, typename XT = T>
+__global__ void __launch_bounds__((NW + 1) * 32, pk_min_blocks<NW, XT>())
     k_schwarz_pk(PkArgs A, const T* __restrict__ r, T* __restrict__ z, T* xglob) {
+  constexpr bool HX = std::is_same<XT, __half>::value;
+  static_assert(SMEMX || std::is_same<XT, T>::value, "a global slice holds the apply's own type");
   extern __shared__ __align__(128) unsigned char pk_smem[];
   __shared__ uint64_t full[NSTAGE], empty[NSTAGE], probe_bar;
   __shared__ int abort_flag;
+  __shared__ float xred[HX ? NW : 1];  // FP16: per-warp maxima of |R_j r|
+  __shared__ T xout;                   // FP16: 1 / (alpha * sigma), set by consumer thread 0
   int64_t issued = 0;  // chunks the producer lane has issued (used by its drain)
   const int j = A.natural ? (int)blockIdx.x : A.order[blockIdx.x], rhs = blockIdx.y;
   const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
@@ -478,8 +521,8 @@ __global__ void __launch_bounds__((NW + 1) * 32, NW == PK_WARPS ? 2 : 4)
   unsigned char* ring = pk_smem;
   uint16_t* csz = reinterpret_cast<uint16_t*>(pk_smem + NSTAGE * CHUNK_BYTES);  // chunk sizes / 16
   const int64_t base = A.sptr[j], n = A.sptr[j + 1] - base;
-  T* xs = SMEMX ? reinterpret_cast<T*>(pk_smem + NSTAGE * CHUNK_BYTES + A.csz_bytes)
-                : xglob + (int64_t)rhs * A.nloc + base;
+  XT* xs = SMEMX ? reinterpret_cast<XT*>(pk_smem + NSTAGE * CHUNK_BYTES + A.csz_bytes)
+                 : reinterpret_cast<XT*>(xglob + (int64_t)rhs * A.nloc + base);
   const int64_t c0 = A.chsub[j], nch = A.chsub[j + 1] - c0;
   for (int64_t c = tid; c < nch; c += blockDim.x) csz[c] = A.csz[c0 + c];
   if (tid == 0) {
@@ -519,9 +562,24 @@ __global__ void __launch_bounds__((NW + 1) * 32, NW == PK_WARPS ? 2 : 4)
       }
     }
   } else {
+    T alpha = 1, sigma = 1;  // FP16 scales (1 otherwise)
+    bool have_sigma = false;
+    if constexpr (HX) {
+      float amax = 0.f;
+      for (int64_t q = tid; q < n; q += NW * 32)
+        if (!(A.transpose && !A.owned[base + q])) amax = fmaxf(amax, fabsf((float)r[A.snode[base + q]]));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+      if (lane == 0) xred[wid] = amax;
+      consumer_sync<NW>();
+      amax = 0.f;
+      for (int w = 0; w < NW; ++w) amax = fmaxf(amax, xred[w]);
+      alpha = pow2_scale(amax);
+    }
     for (int64_t q = tid; q < n; q += NW * 32) {
-      const T v = r[A.snode[base + q]];
-      xs[q] = (A.transpose && !A.owned[base + q]) ? (T)0 : v;
+      T v = r[A.snode[base + q]];
+      if constexpr (HX) v = v * alpha;
+      xs[q] = to_x<XT>((A.transpose && !A.owned[base + q]) ? (T)0 : v);
     }
     consumer_sync<NW>();
     for (int64_t c = 0; c < nch; ++c) {
@@ -546,6 +604,12 @@ __global__ void __launch_bounds__((NW + 1) * 32, NW == PK_WARPS ? 2 : 4)
       if (!__any_sync(0xffffffffu, *(volatile int*)&abort_flag != 0)) {
         constexpr int LPR = SW_LPR, RPW = 32 / LPR;  // lanes per row, rows per warp
         const int e0 = ch.z ? 1 : 0, sub = lane & (LPR - 1);
+        if constexpr (HX) {
+          if (ch.z && !have_sigma && ch.x > 0) {  // the same chunk sets it in every warp
+            sigma = pow2_recip(cvt<V, float>(vals[hdr[0].y]));
+            have_sigma = true;
+          }
+        }
         // rows rb + RPW * wid + lane / LPR; the loop is warp-uniform so that
         // every lane reaches the shuffles
         for (int rb = 0; rb < ch.x; rb += RPW * NW) {
@@ -555,14 +619,18 @@ __global__ void __launch_bounds__((NW + 1) * 32, NW == PK_WARPS ? 2 : 4)
           T sdot = 0;
           if (has) {
             h = hdr[rr];
-            sdot = row_dot<T, V, LPR, (SMEMX ? 4 : 64 / LPR)>(h, e0, sub, vals, cols, xs);
+            sdot = row_dot<T, V, LPR, (SMEMX ? 4 : 64 / LPR), XT>(h, e0, sub, vals, cols, xs);
           }
 #pragma unroll
           for (int o = LPR / 2; o > 0; o >>= 1) sdot += __shfl_xor_sync(0xffffffffu, sdot, o);
           if (has && sub == 0) {
-            T v = xs[h.x] - sdot;
+            T v = cvt<XT, T>(xs[h.x]);
+            if constexpr (HX) {
+              if (ch.z) v = v * sigma;
+            }
+            v = v - sdot;
             if (ch.z) v = v * cvt<V, T>(vals[h.y]);
-            xs[h.x] = v;
+            xs[h.x] = to_x<XT>(v);
           }
         }
       }
@@ -583,6 +651,9 @@ __global__ void __launch_bounds__((NW + 1) * 32, NW == PK_WARPS ? 2 : 4)
         }
       }
     }
+    if constexpr (HX) {
+      if (tid == 0) xout = ((T)1 / alpha) * ((T)1 / sigma);  // powers of two: exact
+    }
   }
   __syncthreads();
   if (abort_flag) {
@@ -602,12 +673,14 @@ __global__ void __launch_bounds__((NW + 1) * 32, NW == PK_WARPS ? 2 : 4)
       }
     return;
   }
+  T unscale = 1;
+  if constexpr (HX) unscale = xout;
   if (!A.transpose) {
     for (int64_t q = tid; q < n; q += blockDim.x)
-      if (A.owned[base + q]) z[A.snode[base + q]] = xs[q];
+      if (A.owned[base + q]) z[A.snode[base + q]] = cvt<XT, T>(xs[q]) * unscale;
   } else if (SMEMX) {
     T* xg = xglob + (int64_t)rhs * A.nloc + base;
-    for (int64_t q = tid; q < n; q += blockDim.x) xg[q] = xs[q];
+    for (int64_t q = tid; q < n; q += blockDim.x) xg[q] = cvt<XT, T>(xs[q]) * unscale;
   }
 }
 
@@ -674,6 +747,10 @@ void packed_free(PackedFactors& pf, cudaStream_t s) {
 // chunk-size table, plus the local vector when it lives in shared memory
 // (at most 113 KB in total, so that two CTAs fit on one SM).
 constexpr size_t PK_SMEM_MAX = 113 * 1024;
+// ... and with an FP16 local vector (one CTA per SM): up to the 227 KB a CTA
+// may have, less a margin for the kernel's static shared memory
+constexpr size_t PK_SMEM_HALF = 226 * 1024;
+constexpr int PK_WARPS_WIDE = 24;  // consumer warps of the FP16 variant with xplace 3
 
 // Raise the kernels' dynamic shared-memory limit once per device (the
 // attribute is a ceiling; each launch asks for what it needs).
@@ -691,6 +768,12 @@ static cpm_status allow_pk_smem(cudaStream_t) {
     CPM_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PK_SMEM_MAX));
   CPM_CUDA(cudaFuncSetAttribute((const void*)k_schwarz_pk<T, V, false, 8, PK_WARPS_FOUR>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PK_SMEM_MAX));
+  if constexpr (std::is_same<T, float>::value) {
+    CPM_CUDA(cudaFuncSetAttribute((const void*)k_schwarz_pk<float, V, true, 8, PK_WARPS, __half>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PK_SMEM_HALF));
+    CPM_CUDA(cudaFuncSetAttribute((const void*)k_schwarz_pk<float, V, true, 8, PK_WARPS_WIDE, __half>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PK_SMEM_HALF));
+  }
   done.fetch_or(bit);
   return CPM_OK;
 }
@@ -701,11 +784,11 @@ static cpm_status allow_pk_smem(cudaStream_t) {
 constexpr int PK_CARVE_ONE = 28;
 constexpr size_t PK_SMEM_ONE = 60 * 1024;
 
-template <typename T, typename V, bool SMEMX, int L, int NW = PK_WARPS>
+template <typename T, typename V, bool SMEMX, int L, int NW = PK_WARPS, typename XT = T>
 static void launch_pk_l(int carve, dim3 g, size_t sm, cudaStream_t s, const PkArgs& A, const T* r, T* z, T* xl) {
   constexpr int NT = (NW + 1) * 32;
-  cudaFuncSetAttribute(k_schwarz_pk<T, V, SMEMX, L, NW>, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
-  KL(k_schwarz_pk<T, V, SMEMX, L, NW><<<g, NT, sm, s>>>(A, r, z, xl));
+  cudaFuncSetAttribute(k_schwarz_pk<T, V, SMEMX, L, NW, XT>, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
+  KL(k_schwarz_pk<T, V, SMEMX, L, NW, XT><<<g, NT, sm, s>>>(A, r, z, xl));
 }
 
 // ctas 4 (global slices only): four CTAs per SM of PK_WARPS_FOUR consumer
@@ -717,6 +800,17 @@ static void launch_pk(int lanes, int ctas, int carve, dim3 g, size_t sm, cudaStr
   else if (lanes == 4) launch_pk_l<T, V, SMEMX, 4>(carve, g, sm, s, A, r, z, xl);
   else if (lanes == 16) launch_pk_l<T, V, SMEMX, 16>(carve, g, sm, s, A, r, z, xl);
   else launch_pk_l<T, V, SMEMX, 8>(carve, g, sm, s, A, r, z, xl);
+}
+
+// FP16 local vector (FP32 applies only): 8 lanes per row, 12 or (wide) 24
+// consumer warps, one CTA per SM
+template <typename T, typename V>
+static void launch_pk_half(bool wide, int carve, dim3 g, size_t sm, cudaStream_t s, const PkArgs& A, const T* r,
+                           T* z, T* xl) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (wide) launch_pk_l<float, V, true, 8, PK_WARPS_WIDE, __half>(carve, g, sm, s, A, r, z, xl);
+    else launch_pk_l<float, V, true, 8, PK_WARPS, __half>(carve, g, sm, s, A, r, z, xl);
+  }
 }
 
 template <typename T, typename V>
@@ -743,30 +837,37 @@ static cpm_status run_pk(const oras_pc* P, const PackedFactors& pf, const T* r, 
   const size_t xsb = (size_t)P->max_rows * sizeof(T);
   // local vector in shared memory when it fits beside the ring with two CTAs
   // per SM, unless the caller asked for the global slice
-  const bool smemx = P->xplace == 0 && ring + xsb <= 113 * 1024;
+  const bool smemx = P->xplace != 1 && ring + xsb <= PK_SMEM_MAX;
+  // else, for FP32 applies with xplace 2 or 3, an FP16 local vector in shared
+  // memory (one CTA per SM) when that fits
+  const bool smemh = std::is_same<T, float>::value && !smemx && (P->xplace == 2 || P->xplace == 3) &&
+                     ring + (size_t)P->max_rows * 2 <= PK_SMEM_HALF;
   // one CTA per SM with a small shared-memory carve-out (the rest of the SM's
   // memory is L1, which then holds most of one subdomain's global slice)
   // CTAs per SM for global slices: one by default (measured 9 % faster than two
   // at h = 0.002, where two 230 KB slices per SM overflow L1)
   const int ctas = P->ctas ? P->ctas : 1;
-  const bool one_cta = !smemx && ctas == 1 && ring <= PK_SMEM_ONE;
-  const bool four = !smemx && ctas == 4 && 4 * ring <= 220 * 1024;
-  const size_t sm = smemx ? ring + xsb : (one_cta ? PK_SMEM_ONE : ring);
-  const int carve = one_cta ? PK_CARVE_ONE : (four ? (int)cudaSharedmemCarveoutMaxShared : (int)cudaSharedmemCarveoutDefault);
-  if (sm > PK_SMEM_MAX) return fail(CPM_ERR_ARG, "Schwarz apply needs %zu bytes of shared memory", sm);
+  const bool one_cta = !smemx && !smemh && ctas == 1 && ring <= PK_SMEM_ONE;
+  const bool four = !smemx && !smemh && ctas == 4 && 4 * ring <= 220 * 1024;
+  const size_t sm = smemh ? ring + pad16((int64_t)P->max_rows * 2)
+                          : (smemx ? ring + xsb : (one_cta ? PK_SMEM_ONE : ring));
+  const int carve = one_cta ? PK_CARVE_ONE
+                            : ((four || smemh) ? (int)cudaSharedmemCarveoutMaxShared : (int)cudaSharedmemCarveoutDefault);
+  if (sm > (smemh ? PK_SMEM_HALF : PK_SMEM_MAX))
+    return fail(CPM_ERR_ARG, "Schwarz apply needs %zu bytes of shared memory", sm);
   CPM_TRY((allow_pk_smem<T, V>(s)));
   T* xloc = nullptr;
-  if (!smemx || transpose) CPM_TRY(dalloc(&xloc, (size_t)nrhs * P->nloc, s));
+  if ((!smemx && !smemh) || transpose) CPM_TRY(dalloc(&xloc, (size_t)nrhs * P->nloc, s));
   for (int r0 = 0; r0 < nrhs; r0 += 65535) {
     const int nr = nrhs - r0 < 65535 ? nrhs - r0 : 65535;
     dim3 g(P->np, nr);
     T* xl = xloc ? xloc + (int64_t)r0 * P->nloc : nullptr;
     const int lanes = P->lanes ? P->lanes : (smemx ? SW_LPR_SMEM : SW_LPR_GLOBAL);
-    if (smemx)
-      launch_pk<T, V, true>(lanes, 0, carve, g, sm, s, A, r + (int64_t)r0 * P->nA, z + (int64_t)r0 * P->nA, xl);
-    else
-      launch_pk<T, V, false>(lanes, four ? 4 : 0, carve, g, sm, s, A, r + (int64_t)r0 * P->nA,
-                             z + (int64_t)r0 * P->nA, xl);
+    const T* rr = r + (int64_t)r0 * P->nA;
+    T* zz = z + (int64_t)r0 * P->nA;
+    if (smemh) launch_pk_half<T, V>(P->xplace == 3, carve, g, sm, s, A, rr, zz, xl);
+    else if (smemx) launch_pk<T, V, true>(lanes, 0, carve, g, sm, s, A, rr, zz, xl);
+    else launch_pk<T, V, false>(lanes, four ? 4 : 0, carve, g, sm, s, A, rr, zz, xl);
     if (transpose) {
       dim3 g2(grid_for(P->nA, 256), nr);
       KL(k_gather_T2<T><<<g2, 256, 0, s>>>(P->nA, P->nloc, P->mcnt, P->mloc, xl, z + (int64_t)r0 * P->nA));

@@ -313,6 +313,59 @@ def test_schwarz_large_subdomains_multichunk_levels(cpm, oracle_mod, torus0025):
         assert _rel(ZT[q], OP.apply(R[q], transpose=True)) <= 1e-12
 
 
+# FP16 local vector (xplace 2 and 3): every stored sweep value is rounded to 11
+# significant bits (relative error <= 2^-11) after a power-of-two scaling that
+# keeps it in FP16's normal range; the sweeps' growth (below 3 on these bands)
+# and ~60-entry rows bound the apply's error at a few 1e-3 of max|z|.  1e-2
+# fails any wrong entry, level, scale or row (those give errors of order 1).
+HALF_TOL = 1e-2
+
+
+@pytest.mark.parametrize("xplace", [2, 3])
+def test_schwarz_half_local_vector_matches_oracle(cpm, oracle_mod, torus0025, xplace):
+    """~38k-row subdomains with an FP16 local vector in shared memory (FP32 and
+    BF16 factors, forward and transposed, two right-hand sides) against the
+    oracle; FP64 applies ignore the setting."""
+    B, O, M, OP = torus0025
+    R = np.stack([inputs.gaussian_vector(40 + q, B.n_active) for q in range(2)])
+    # one right-hand side scaled far down: the per-subdomain power-of-two scale
+    # must bring it back into FP16's range
+    R[1] *= 1e-9
+    want = [OP.apply(R[q]) for q in range(2)]
+    wantT = [OP.apply(R[q], transpose=True) for q in range(2)]
+    for store, tol in ((cpm.CPM_F32, HALF_TOL), (cpm.CPM_BF16, BF16_TOL + HALF_TOL)):
+        P = cpm.Schwarz(B, 10.0, 4, 2, store=store)
+        P.set_tuning(xplace=xplace)
+        Z = P.apply(_cuda(R).reshape(-1).float()).double().cpu().numpy().reshape(2, -1)
+        ZT = P.apply(_cuda(R).reshape(-1).float(), transpose=True).double().cpu().numpy().reshape(2, -1)
+        for q in range(2):
+            assert np.all(np.isfinite(Z[q])) and np.all(np.isfinite(ZT[q]))
+            assert _rel(Z[q], want[q]) <= tol
+            assert _rel(ZT[q], wantT[q]) <= tol
+        Z64 = P.apply(_cuda(R[0])).cpu().numpy()
+        assert _rel(Z64, want[0]) <= 1e-12
+
+
+def test_mixed_solve_with_half_local_vector(cpm, oracle_mod, torus0025):
+    """The flexible mixed-precision solve with the FP16 local vector reaches
+    the same tolerance as with the FP32 one, in at most a few more
+    iterations, and its solution satisfies sampled rows of the oracle's M."""
+    B, O, M, OP = torus0025
+    f = inputs.gaussian_vector(44, B.n_active)
+    P = cpm.Schwarz(B, 10.0, 4, 2, store=cpm.CPM_F32)
+    u32, i32 = cpm.solve(B, _cuda(f), P, rtol=1e-9, mixed=True, maxit=5000)
+    P.set_tuning(xplace=2)
+    u16, i16 = cpm.solve(B, _cuda(f), P, rtol=1e-9, mixed=True, maxit=5000)
+    assert i32["status"] == 0 and i16["status"] == 0
+    assert i16["rel_residual"] <= 1e-9
+    assert i16["iters"] <= 1.1 * i32["iters"] + 3
+    un = u16.cpu().numpy()
+    rows = np.arange(0, B.n_active, 97)
+    res = O.apply_rows(10.0, un, rows) - f[rows]
+    assert np.abs(res).max() <= 1e-8 * np.linalg.norm(f)
+    assert np.linalg.norm(un - u32.cpu().numpy()) <= 1e-6 * np.linalg.norm(un)
+
+
 def test_schwarz_timeout_is_reported_and_recovers(cpm, oracle_mod, torus005, torus005_lu):
     """Failure path of the bounded waits, without a GPU fault: with the probe
     on, the first chunk wait of every subdomain waits on a barrier nothing
