@@ -480,12 +480,18 @@ cpm_status apply_typed(const cpm_band* B, const double* c, const T* x, T* y, int
   if (transpose && !B->tptr) CPM_TRY(build_transpose_map(const_cast<cpm_band*>(B), s));
   for (int r0 = 0; r0 < nrhs; r0 += MAXRHS) {
     int nr = nrhs - r0 < MAXRHS ? nrhs - r0 : MAXRHS;
+    const T* xr = x + (int64_t)r0 * B->nA;
+    T* yr = y + (int64_t)r0 * B->nA;
+    if constexpr (sizeof(T) == 4) {
+      if (!transpose && B->ntile > 0) {  // staged through shared memory by bricks (tile.cu)
+        CPM_TRY(tile_apply_f32(B, c + r0, xr, yr, nr, s));
+        continue;
+      }
+    }
     Shifts S{};
     for (int q = 0; q < nr; ++q) S.c[q] = c[r0 + q];
     T* w = nullptr;
     CPM_TRY(dalloc(&w, (size_t)nr * B->nR * (sizeof(T) == 4 ? 2 : 1), s));
-    const T* xr = x + (int64_t)r0 * B->nA;
-    T* yr = y + (int64_t)r0 * B->nA;
     if (!transpose) {
       CPM_TRY(erow_pass(B, G, xr, w, nr, s));
       dim3 g2(grid_for(B->nA, 256), nr);

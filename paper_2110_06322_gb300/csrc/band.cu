@@ -357,6 +357,7 @@ cpm_status band_build(const cpm_surface* surf, double h, int p, cudaStream_t s, 
   CPM_CUDA(cudaStreamSynchronize(s));
   if (herr) return cleanup(fail(CPM_ERR_BAND, "an interpolation cube is not inside the active set"));
   if ((st = build_erow_groups(B, s)) != CPM_OK) return cleanup(st);
+  if ((st = build_tiles(B, s)) != CPM_OK) return cleanup(st);
   *out = B;
   return cleanup(CPM_OK);
 }
@@ -380,6 +381,7 @@ void band_free(cpm_band* B, cudaStream_t s) {
   dfree(B->gitem, s);
   dfree(B->grow, s);
   dfree(B->grec, s);
+  free_tiles(B, s);
   if (B->wbuf) cudaFreeAsync(B->wbuf, s);
   B->wbuf = nullptr;
   delete B;

@@ -149,6 +149,14 @@ struct cpm_band {
   int32_t* grow = nullptr;       // [nR] E rows in cube-base order (set-up only)
   float* grec = nullptr;         // [nR][4] per row in that order: FP32 offsets s_x, s_y, s_z and the row
                                  // index (as the bits of the fourth float), one 16-byte record
+  // tile-staged FP32 apply: bricks of 16^3 cells holding active nodes, each
+  // with the E rows its stencils need, grouped by cube
+  int64_t ntile = 0, ntrec = 0;
+  int32_t* thead = nullptr;      // [ntile][8] brick origin, work items, box origin, box extents
+  int64_t* troff = nullptr;      // [ntile + 1] first record of each brick
+  float* trec = nullptr;         // [ntrec][4] {s_x, s_y, s_z, slot of the row in the grown brick (bits)}
+  uint32_t* titem = nullptr;     // [ntrec] work items (the first nitem of each brick's range)
+  int32_t tmaxbox = 0;           // cells of the largest box
   // scratch for the operator apply
   void* wbuf = nullptr;          // [nR] E x values (FP64 room)
   size_t wbuf_bytes = 0;

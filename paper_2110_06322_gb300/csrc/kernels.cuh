@@ -25,6 +25,10 @@ cpm_status apply_op(const cpm_band* B, const double* c, const void* x, void* y, 
 cpm_status build_transpose_map(cpm_band* B, cudaStream_t s);
 // group the E rows by interpolation cube for the FP32 apply (band build)
 cpm_status build_erow_groups(cpm_band* B, cudaStream_t s);
+// tile.cu: the FP32 forward apply staged through shared memory by bricks
+cpm_status build_tiles(cpm_band* B, cudaStream_t s);
+void free_tiles(cpm_band* B, cudaStream_t s);
+cpm_status tile_apply_f32(const cpm_band* B, const double* c, const float* x, float* y, int nrhs, cudaStream_t s);
 cpm_status apply_op_scratch(const cpm_band* B, const double* c, const void* x, void* y, cpm_dtype dt, int nrhs,
                             void* scratch, cudaStream_t s);
 

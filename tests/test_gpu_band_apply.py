@@ -85,6 +85,19 @@ def test_apply_several_rhs_with_their_own_shift(cpm, oracle_mod):
         assert np.abs(Y[q] - want).max() <= 1e-14 * np.abs(want).max()
 
 
+def test_fp32_apply_of_18_rhs_with_their_own_shift(cpm, oracle_mod):
+    """The FP32 forward apply (staged by bricks) over more right-hand sides
+    than one launch takes (16), each with its own shift."""
+    B = cpm.Band(0, (0.013, 0.1, -0.07, 0.7), 0.03, 3)
+    O = oracle_mod.Band(0, (0.013, 0.1, -0.07, 0.7), 0.03, 3)
+    cs = [0.1 * 2.0 ** q for q in range(18)]
+    X = np.stack([inputs.gaussian_vector(60 + q, B.n_active) for q in range(18)])
+    Y = B.apply(cs, torch.from_numpy(X).float().cuda().reshape(-1)).double().cpu().numpy().reshape(18, -1)
+    for q, c in enumerate(cs):
+        want = O.M(c).matvec(X[q])
+        assert np.abs(Y[q] - want).max() <= 2e-6 * np.abs(want).max()
+
+
 def test_constant_is_mapped_to_c(cpm):
     B = cpm.Band(1, TOR, 0.01, 3)
     y = B.apply(7.0, torch.ones(B.n_active, dtype=torch.float64, device="cuda"))
