@@ -20,8 +20,8 @@
 //      x_ref) + (x_ref - x_i), with x_ref the cube's node (1,1,1));
 //   3. forms the stencil of each active node from that grid and writes y.
 // No intermediate goes through HBM and no gather needs a bitmap lookup.  The
-// per-row arithmetic and the stencil's sum order are those of the two-pass
-// FP32 apply.  Rows that neighbour two bricks are evaluated by both (about
+// contraction order of a row and the stencil's sum order are those of the
+// two-pass FP32 apply.  Rows that neighbour two bricks are evaluated by both (about
 // a fifth more rows than N_C at TB = 16).
 //
 // Set-up (band build): bricks holding active nodes are listed in canonical
@@ -261,18 +261,22 @@ __global__ void __launch_bounds__(TBUILD_THREADS) k_tb_build(TileBuildArgs A) {
 }
 
 // ---------------------------------------------------------------- apply
+// Lagrange weights of nodes 0..P at s (product form).  The denominators are
+// constants, so each weight is scaled by the rounded reciprocal of its
+// denominator (one multiply instead of an IEEE division; at most an ulp apart).
 template <int P>
 __device__ __forceinline__ void tile_lagrange(float s, float* l) {
 #pragma unroll
   for (int j = 0; j <= P; ++j) {
-    float num = 1.0f, den = 1.0f;
+    float num = 1.0f;
+    int den = 1;
 #pragma unroll
     for (int k = 0; k <= P; ++k)
       if (k != j) {
         num *= (s - (float)k);
-        den *= (float)(j - k);
+        den *= j - k;
       }
-    l[j] = num / den;
+    l[j] = num * (1.0f / (float)den);
   }
 }
 
