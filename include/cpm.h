@@ -199,7 +199,7 @@ cpm_status oras_apply(const oras_pc* pc, const void* r, void* z, cpm_dtype dtype
  *                  in shared memory (one CTA per SM, 8 lanes per row, 12
  *                  consumer warps) when that fits: the entries of R_j r are
  *                  scaled by a power of two per subdomain so the largest is
- *                  below 2^10, and rows that carry a reciprocal pivot are
+ *                  in [1, 2), and rows that carry a reciprocal pivot are
  *                  computed as (x_i sigma - sum) / pivot with a power of two
  *                  sigma near the pivot, so stored values stay in FP16's normal
  *                  range; arithmetic stays FP32.  This changes the
