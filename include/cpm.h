@@ -318,9 +318,11 @@ cpm_status cpm_solve_adjoint(const cpm_band* band, const oras_pc* pc, double c, 
  * on the device when its residual estimate reaches rtol |f| and is frozen
  * until the others finish their cycle; each cycle ends with every system's
  * true FP64 residual.  mixed = 1 runs the operator and preconditioner in FP32
- * inside FP64 iterative refinement (FP32 or BF16 factors required).
+ * inside FP64 iterative refinement (FP32 or BF16 factors required), each
+ * inner cycle flexible (the correction is sum_j y_j P v_j over the kept
+ * preconditioned vectors).
  * The lockstep solver keeps (restart + 7) doubles per unknown of every system
- * it runs at once, so the problems are cut, in order, into consecutive
+ * it runs at once (2 restart + 7 with mixed = 1), so the problems are cut, in order, into consecutive
  * groups whose storage fits min(32 GB, 40 % of the device's free memory),
  * solved one group after another within the call.
  * Returns CPM_ERR_NOT_CONVERGED if any system missed rtol within maxit

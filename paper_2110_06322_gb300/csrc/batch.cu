@@ -23,8 +23,8 @@
 // The operator and the preconditioner apply once per problem per iteration,
 // with all its right-hand sides in one launch; the problems' launches go to
 // eight side streams, so that small problems run side by side.  With mixed = 1 they run in
-// FP32 inside FP64 iterative refinement (one inner cycle per refinement
-// step), exactly as cpm_solve does for one system.
+// FP32 inside FP64 iterative refinement (one flexible inner cycle per
+// refinement step), as cpm_solve does for one system.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -280,6 +280,11 @@ struct Batch {
   Seg GA{};  // blocks of stopped systems skip (act = X.active)
   int32_t* sb = nullptr;  // [S+1] first block of each system
   double *V = nullptr, *w = nullptr, *z = nullptr, *t = nullptr, *r = nullptr, *ny = nullptr, *partial = nullptr;
+  // mixed precision: the preconditioned vectors z_j = P v_j of the inner
+  // cycle (m x N), kept so that the correction is sum_j y_j z_j (flexible
+  // GMRES): it is built from exactly the vectors of the Arnoldi relation, and
+  // the cycle needs no preconditioner apply after the last column
+  double* Z = nullptr;
   float *x32 = nullptr, *y32 = nullptr;
   SysState X{};
   std::vector<void*> owned;
@@ -432,8 +437,9 @@ cpm_status batch_P(Batch& Bt, const double* x, double* out, bool f32, int transp
   return Bt.fan_in(s);
 }
 
-// One GMRES(m) cycle for every active system on M d = b (x += P V y), from
-// the residual vector r (overwritten).  inner: tolerances relative to |r|
+// One GMRES(m) cycle for every active system on M d = b (x += P V y, or
+// x += Z y with the kept z_j = P v_j in the mixed cycle), from the residual
+// vector r (overwritten).  inner: tolerances relative to |r|
 // (refinement), else to |f|.
 cpm_status batch_cycle(Batch& Bt, double* x, bool f32, int transpose, int maxit, double rtol, int inner,
                        cudaStream_t s) {
@@ -443,10 +449,12 @@ cpm_status batch_cycle(Batch& Bt, double* x, bool f32, int transpose, int maxit,
   CPM_TRY(seg_dots(Bt, Bt.G, Bt.r, 1, Bt.r, Bt.X.rr, 1, 0, s));
   KL(kb_cycle_init<<<gs, 128, 0, s>>>(S, m, Bt.X, maxit, rtol, inner));
   KL(kb_scale<<<Bt.NB, RED_THREADS, 0, s>>>(Bt.G, Bt.r, Bt.X.scale, Bt.V));
+  const bool flex = f32 && Bt.Z;
   for (int j = 0; j < m; ++j) {
     double* vj = Bt.V + (int64_t)j * Bt.N;
-    CPM_TRY(batch_P(Bt, vj, Bt.z, f32, transpose, s));
-    CPM_TRY(batch_M(Bt, Bt.z, Bt.w, f32, transpose, s));
+    double* zj = flex ? Bt.Z + (int64_t)j * Bt.N : Bt.z;
+    CPM_TRY(batch_P(Bt, vj, zj, f32, transpose, s));
+    CPM_TRY(batch_M(Bt, zj, Bt.w, f32, transpose, s));
     // classical Gram-Schmidt, one pass: hc = V^T w; w -= V hc; hc[j+1] = |w|^2
     const int nv = j + 1, cs = chunk_of(nv);
     for (int t0 = 0; t0 < nv; t0 += cs) {
@@ -463,16 +471,21 @@ cpm_status batch_cycle(Batch& Bt, double* x, bool f32, int transpose, int maxit,
     if (j + 1 < m) KL(kb_scale<<<Bt.NB, RED_THREADS, 0, s>>>(Bt.GA, Bt.w, Bt.X.scale, Bt.V + (int64_t)(j + 1) * Bt.N));
     CPM_CUDA(cudaGetLastError());
   }
-  // x += P (V y), y per system over its kk columns
+  // x += P (V y), or x += Z y when flexible; y per system over its kk columns
   KL(kb_trisolve<<<gs, 128, 0, s>>>(S, m, Bt.X, Bt.ny, m));
   CPM_CUDA(cudaMemsetAsync(Bt.t, 0, Bt.N * sizeof(double), s));
   const int cs = chunk_of(m);
+  const double* basis = flex ? Bt.Z : Bt.V;
   for (int t0 = 0; t0 < m; t0 += cs) {
     const int nc = std::min(cs, m - t0);
-    CPM_TRY(seg_update(Bt, Bt.G, Bt.V + (int64_t)t0 * Bt.N, nc, Bt.ny + t0, m, Bt.t, false, nullptr, 0, s));
+    CPM_TRY(seg_update(Bt, Bt.G, basis + (int64_t)t0 * Bt.N, nc, Bt.ny + t0, m, Bt.t, false, nullptr, 0, s));
   }
-  CPM_TRY(batch_P(Bt, Bt.t, Bt.z, f32, transpose, s));
-  KL(kb_axpy<<<grid_n(Bt.N), 256, 0, s>>>(Bt.z, x, Bt.N));
+  if (flex) {
+    KL(kb_axpy<<<grid_n(Bt.N), 256, 0, s>>>(Bt.t, x, Bt.N));
+  } else {
+    CPM_TRY(batch_P(Bt, Bt.t, Bt.z, f32, transpose, s));
+    KL(kb_axpy<<<grid_n(Bt.N), 256, 0, s>>>(Bt.z, x, Bt.N));
+  }
   CPM_CUDA(cudaGetLastError());
   return CPM_OK;
 }
@@ -576,6 +589,10 @@ cpm_status solve_group(int nprob, const cpm_band* const* bands, const oras_pc* c
   if (mixed) {
     BTRY(Bt.get(&Bt.x32, Bt.N, s));
     BTRY(Bt.get(&Bt.y32, Bt.N, s));
+    // finished problems' columns keep finite values (these zeros or older
+    // vectors) and enter the correction with coefficient 0
+    BTRY(Bt.get(&Bt.Z, (size_t)m * Bt.N, s));
+    BTRY(cudaMemsetAsync(Bt.Z, 0, (size_t)m * Bt.N * sizeof(double), s) == cudaSuccess ? CPM_OK : CPM_ERR_CUDA);
   }
   SysState& X = Bt.X;
   BTRY(Bt.get(&X.H, (size_t)S * (m + 1) * m, s));
@@ -687,7 +704,8 @@ cpm_status solve_group(int nprob, const cpm_band* const* bands, const oras_pc* c
 }  // namespace
 
 // Memory-bounded batching: the lockstep solver holds its Krylov basis and
-// work vectors for every system at once ((restart + 7) doubles per unknown),
+// work vectors for every system at once ((restart + 7) doubles per unknown,
+// 2 restart + 7 with the preconditioned vectors of the mixed cycle),
 // so the problems are cut, in order, into consecutive groups whose storage
 // fits min(32 GB, 40 % of the device's free memory) and the groups are
 // solved one after another.
@@ -697,7 +715,7 @@ cpm_status solve_batch(int nprob, const cpm_band* const* bands, const oras_pc* c
   size_t freeb = 0, totalb = 0;
   CPM_CUDA(cudaMemGetInfo(&freeb, &totalb));
   const double budget = std::min(32e9, 0.4 * (double)freeb);
-  const double per_unknown = 8.0 * (prm->restart + 7);
+  const double per_unknown = 8.0 * ((prm->mixed ? 2 * prm->restart : prm->restart) + 7);
   cpm_status all = CPM_OK;
   int p0 = 0;
   int64_t off = 0, sys0 = 0;

@@ -81,9 +81,10 @@ WORKLOADS = {
     "torus_h0.025": dict(kind=TORUS, params=surface_params(TORUS, a=1.0, b=0.4), h=0.025, p=3, c=10.0,
                          rhs="modes", seed=2, nparts=16, overlap=2, robin=False, restart=30, rtol=1e-8,
                          solve_rtol=1e-8, order=2),
+    # xplace 3: the subdomains (~58k rows) hold their local vectors in FP16 in shared memory
     "torus_h0.002": dict(kind=TORUS, params=surface_params(TORUS, a=1.0, b=0.4), h=0.002, p=3, c=10.0,
                          rhs="modes", seed=3, nparts=512, overlap=2, robin=False, alpha=4.0, alpha_cross=20.0,
-                         restart=30, rtol=1e-8, solve_rtol=1e-8, order=2),
+                         restart=30, rtol=1e-8, solve_rtol=1e-8, order=2, xplace=3),
     # differentiable Schnakenberg run (eq. schnack): D = (1e-3, 1e-1), dt = 0.01, 500 steps, state
     # checkpoints every 25 steps; initial state (u*, v*) (1 + 0.01 U[-1, 1]) from seed 7 (u) and 8 (v)
     "schnakenberg_torus_h0.005": dict(kind=TORUS, params=surface_params(TORUS, a=1.0, b=0.4), h=0.005, p=3,
