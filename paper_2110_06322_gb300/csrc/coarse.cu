@@ -39,7 +39,7 @@ constexpr int NBMAX = 64;  // parts one part's rows reach, summed warp-parallel 
 // each.  count pass (out == nullptr) or fill pass.
 __global__ void k_mz(int64_t nA, const int64_t* __restrict__ mptr, const int32_t* __restrict__ mcol,
                      const double* __restrict__ mval, const int32_t* __restrict__ part, int32_t* cnt,
-                     const int64_t* __restrict__ optr, int32_t* opart, double* oval, float* oval32, int* err) {
+                     const int64_t* __restrict__ optr, int32_t* opart, double* oval, int* err) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nA; i += (int64_t)gridDim.x * blockDim.x) {
     int32_t pp[KMZ];
     double vv[KMZ];
@@ -66,7 +66,6 @@ __global__ void k_mz(int64_t nA, const int64_t* __restrict__ mptr, const int32_t
       for (int t = 0; t < k; ++t) {
         opart[o + t] = pp[t];
         oval[o + t] = vv[t];
-        oval32[o + t] = (float)vv[t];
       }
     }
   }
@@ -264,10 +263,14 @@ __global__ void k_coarse_mv(int np, const double* __restrict__ Einv, const doubl
   if (lane == 0) y[(int64_t)rhs * np + row] = acc;
 }
 
-// t_i = r_i - (M Z y)_i, the residual left after the coarse correction
+// t_i = r_i - (M Z y)_i, the residual left after the coarse correction.  The
+// coefficients and the sum stay FP64 in FP32 applies too: y is of size |r| / c
+// on the coarse space, so (M Z y)_i cancels against r_i to a value ~c / |M|
+// times its terms, and FP32-rounded coefficients would leave an error of
+// eps_32 |M| / c relative to t (percents for small shifts on fine grids).
 template <typename T>
 __global__ void k_coarse_res(int64_t nA, int np, const int64_t* __restrict__ mzptr, const int32_t* __restrict__ mzpart,
-                             const T* __restrict__ mzval, const double* __restrict__ y, const T* __restrict__ r,
+                             const double* __restrict__ mzval, const double* __restrict__ y, const T* __restrict__ r,
                              T* __restrict__ t) {
   const int rhs = blockIdx.y;
   r += (int64_t)rhs * nA;
@@ -275,7 +278,7 @@ __global__ void k_coarse_res(int64_t nA, int np, const int64_t* __restrict__ mzp
   y += (int64_t)rhs * np;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nA; i += (int64_t)gridDim.x * blockDim.x) {
     double acc = 0.0;
-    for (int64_t e = mzptr[i]; e < mzptr[i + 1]; ++e) acc += (double)mzval[e] * y[mzpart[e]];
+    for (int64_t e = mzptr[i]; e < mzptr[i + 1]; ++e) acc += mzval[e] * y[mzpart[e]];
     t[i] = (T)((double)r[i] - acc);
   }
 }
@@ -297,7 +300,6 @@ cpm_status coarse_apply_t(const oras_pc* P, const T* r, T* z, int nrhs, int tran
   const cpm_dtype dt = sizeof(T) == 8 ? CPM_F64 : CPM_F32;
   const int np = P->np;
   const int64_t nA = P->nA;
-  const T* mzv = sizeof(T) == 8 ? (const T*)P->mzval : (const T*)P->mzval32;
   T* t = nullptr;
   double* y = nullptr;
   CPM_TRY(dalloc(&t, (size_t)nrhs * nA, s));
@@ -311,7 +313,7 @@ cpm_status coarse_apply_t(const oras_pc* P, const T* r, T* z, int nrhs, int tran
   if (!transpose) {
     KL(k_restrict<T><<<gP, 256, 0, s>>>(np, nA, P->sptr, P->snode, P->owned, r, nullptr, y0));
     KL(k_coarse_mv<<<gC, 256, 0, s>>>(np, P->E0inv, y0, y, 0));
-    KL(k_coarse_res<T><<<gN, 256, 0, s>>>(nA, np, P->mzptr, P->mzpart, mzv, y, r, t));
+    KL(k_coarse_res<T><<<gN, 256, 0, s>>>(nA, np, P->mzptr, P->mzpart, P->mzval, y, r, t));
     st = oras_run_one_level(P, t, z, dt, nrhs, 0, s);
     if (st == CPM_OK) KL(k_coarse_add<T><<<gN, 256, 0, s>>>(nA, np, P->part, y, nullptr, z));
   } else {
@@ -359,15 +361,14 @@ cpm_status coarse_build(oras_pc* P, const int64_t* mptr, const int32_t* mcol, co
   if ((st = dalloc(&P->mzptr, nA + 1, s)) != CPM_OK) return done(st);
   CPM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
   const int G = grid_for(nA, 256);
-  KL(k_mz<<<G, 256, 0, s>>>(nA, mptr, mcol, mval, P->part, cnt, nullptr, nullptr, nullptr, nullptr, err));
+  KL(k_mz<<<G, 256, 0, s>>>(nA, mptr, mcol, mval, P->part, cnt, nullptr, nullptr, nullptr, err));
   if ((st = scan_exclusive_i32(cnt, P->mzptr, nA, s)) != CPM_OK) return done(st);
   int64_t nmz = 0;
   CPM_CUDA(cudaMemcpyAsync(&nmz, P->mzptr + nA, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   CPM_CUDA(cudaStreamSynchronize(s));
   if ((st = dalloc(&P->mzpart, nmz, s)) != CPM_OK) return done(st);
   if ((st = dalloc(&P->mzval, nmz, s)) != CPM_OK) return done(st);
-  if ((st = dalloc(&P->mzval32, nmz, s)) != CPM_OK) return done(st);
-  KL(k_mz<<<G, 256, 0, s>>>(nA, mptr, mcol, mval, P->part, nullptr, P->mzptr, P->mzpart, P->mzval, P->mzval32, err));
+  KL(k_mz<<<G, 256, 0, s>>>(nA, mptr, mcol, mval, P->part, nullptr, P->mzptr, P->mzpart, P->mzval, err));
   // E0 and its inverse
   const int64_t nn = (int64_t)np * np;
   if ((st = dalloc(&E, nn, s)) != CPM_OK) return done(st);
@@ -399,7 +400,6 @@ void coarse_free(oras_pc* P, cudaStream_t s) {
   dfree(P->mzptr, s);
   dfree(P->mzpart, s);
   dfree(P->mzval, s);
-  dfree(P->mzval32, s);
   dfree(P->E0inv, s);
 }
 

@@ -85,7 +85,6 @@ struct oras_pc {
   int64_t* mzptr = nullptr;   // [nA+1] rows of M Z: the parts each node's row reaches
   int32_t* mzpart = nullptr;  // [nmz] part
   double* mzval = nullptr;    // [nmz] the row's sum over that part (FP64)
-  float* mzval32 = nullptr;   // [nmz] the same in FP32
   double* E0inv = nullptr;    // [np][np] inverse of Z^T M Z, row-major
 };
 
