@@ -70,9 +70,9 @@ E2E_STEPS = 3      # end-to-end steps (host buffers): at most this many
 # per SM, consumers meeting at level ends): 21,017,388,288 + 541,374,464 bytes over 3,232,543,691
 # entries.  Re-measure when the kernel or its default settings change.
 SCHWARZ_DRAM_PER_ENTRY = (21017388288 + 541374464) / 3232543691
-# The same for the headline's FP16-local-vector kernel (k_schwarz_pk<float, float, 1, 8, 24, __half>);
-# None until captured.
-SCHWARZ_HALF_DRAM_PER_ENTRY = None
+# The same for the headline's FP16-local-vector kernel (k_schwarz_pk<float, float, 1, 8, 24, __half>,
+# local vectors in shared memory): 20,722,704,896 + 172,240,640 bytes over the same entries.
+SCHWARZ_HALF_DRAM_PER_ENTRY = (20722704896 + 172240640) / 3232543691
 
 
 def parse(argv=None):
@@ -92,11 +92,20 @@ def parse(argv=None):
                     help="--workload schnakenberg: also check dL/dD_u, dL/dD_v of a run of this many steps "
                          "against central differences (solves at --rtol)")
     ap.add_argument("--rtol", type=float, default=None, help="--workload schnakenberg: solve tolerance")
+    ap.add_argument("--xplace", type=int, default=None,
+                    help="local-vector placement of the workload's Schwarz applies (oras_tuning.xplace), "
+                         "instead of the workload's own")
     return ap.parse_args(argv)
 
 
+_XPLACE = None  # --xplace
+
+
 def workload(name):
-    return dict(inputs.WORKLOADS[name])
+    w = dict(inputs.WORKLOADS[name])
+    if _XPLACE is not None:
+        w["xplace"] = _XPLACE
+    return w
 
 
 def rhs_pair(cp, w):
@@ -756,7 +765,9 @@ def run_profile(args):
 
 
 def main():
+    global _XPLACE
     args = parse()
+    _XPLACE = args.xplace
     if args.impl == "reference":
         run_reference(args)
     elif args.profile:
