@@ -200,8 +200,9 @@ cpm_status oras_apply(const oras_pc* pc, const void* r, void* z, cpm_dtype dtype
  *                  consumer warps) when that fits: the entries of R_j r are
  *                  scaled by a power of two per subdomain so the largest is
  *                  in [1, 2), and rows that carry a reciprocal pivot are
- *                  computed as (x_i sigma - sum) / pivot with a power of two
- *                  sigma near the pivot, so stored values stay in FP16's normal
+ *                  computed as (x_i sigma - sum) / pivot with sigma the power
+ *                  of two at the binade of c + 6/h^2 (the pivots lie within a
+ *                  small factor of it), so stored values stay in FP16's normal
  *                  range; arithmetic stays FP32.  This changes the
  *                  preconditioner's rounding (about 1e-3 relative), not the
  *                  method; the FP32 inner cycles of the mixed solver are

@@ -29,6 +29,7 @@
 // can still be in flight, since every earlier copy into a stage was waited
 // for by the consumers before the stage was refilled.
 #include <algorithm>
+#include <cmath>
 #include <type_traits>
 #include <vector>
 
@@ -420,13 +421,6 @@ __device__ __forceinline__ float pow2_scale(float amax) {
   const int k = max(-120, min(120, XS_EXP + 126 - be));
   return __int_as_float((127 + k) << 23);
 }
-// the power of two sigma with sigma * d in [1, 2) for a nonzero finite d
-// (d: the reciprocal pivot of a backward row); 1 otherwise
-__device__ __forceinline__ float pow2_recip(float d) {
-  const int be = (__float_as_int(fabsf(d)) >> 23) & 0xff;
-  if (be == 0 || be >= 254) return 1.f;
-  return __int_as_float((254 - be) << 23);
-}
 
 struct PkArgs {
   const int32_t* order;  // subdomains by decreasing chunk count (longest first)
@@ -444,6 +438,7 @@ struct PkArgs {
   uint32_t wait_limit;  // polls of each consumer-side wait before it gives up
   int probe;            // failure-path test: the first chunk wait waits on a barrier nothing completes
   int natural;          // subdomains in partition order instead of longest first
+  float xsigma;         // FP16 local vector: power of two at the binade of the diagonal scale c + 6/h^2
 };
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -495,10 +490,12 @@ constexpr int SW_LPR_GLOBAL = 8;  // global slice: 8 also measured best (4 lanes
 // XT is the type of the local vector: T, or FP16 (in shared memory only, for
 // FP32 applies whose subdomains do not fit there in FP32).  With FP16 the
 // entries of R_j r are scaled by alpha (pow2_scale) and the rows that carry a
-// reciprocal pivot d compute (x_i * sigma - sum) * d, with sigma = pow2_recip
-// of the first such row's d, so that their results (x_i / pivot ~ 1e-6 x_i on
-// the benchmark grids) stay in FP16's normal range; the output is unscaled by
-// 1 / (alpha * sigma), both powers of two.
+// reciprocal pivot d compute (x_i * sigma - sum) * d, with sigma the power of
+// two at the binade of the diagonal scale c + 6/h^2 (the ILU(0) pivots lie
+// within a small factor of it), so that their results (x_i / pivot ~ 1e-6 x_i
+// on the benchmark grids) stay in FP16's normal range; the output is unscaled
+// by 1 / (alpha * sigma), both powers of two.  sigma comes from the host, so
+// the rounding does not depend on the order of rows within a level.
 template <int NW, typename XT>
 constexpr int pk_min_blocks() {
   return NW == PK_WARPS_FOUR ? 4 : (std::is_same<XT, __half>::value ? 1 : 2);
@@ -565,8 +562,8 @@ __global__ void __launch_bounds__((NW + 1) * 32, pk_min_blocks<NW, XT>())
     }
   } else {
     T alpha = 1, sigma = 1;  // FP16 scales (1 otherwise)
-    bool have_sigma = false;
     if constexpr (HX) {
+      sigma = A.xsigma;
       float amax = 0.f;
       for (int64_t q = tid; q < n; q += NW * 32)
         if (!(A.transpose && !A.owned[base + q])) amax = fmaxf(amax, fabsf((float)r[A.snode[base + q]]));
@@ -606,12 +603,6 @@ __global__ void __launch_bounds__((NW + 1) * 32, pk_min_blocks<NW, XT>())
       if (!__any_sync(0xffffffffu, *(volatile int*)&abort_flag != 0)) {
         constexpr int LPR = SW_LPR, RPW = 32 / LPR;  // lanes per row, rows per warp
         const int e0 = ch.z ? 1 : 0, sub = lane & (LPR - 1);
-        if constexpr (HX) {
-          if (ch.z && !have_sigma && ch.x > 0) {  // the same chunk sets it in every warp
-            sigma = pow2_recip(cvt<V, float>(vals[hdr[0].y]));
-            have_sigma = true;
-          }
-        }
         // rows rb + RPW * wid + lane / LPR; the loop is warp-uniform so that
         // every lane reaches the shuffles
         for (int rb = 0; rb < ch.x; rb += RPW * NW) {
@@ -835,6 +826,11 @@ static cpm_status run_pk(const oras_pc* P, const PackedFactors& pf, const T* r, 
   A.wait_limit = P->wait_polls > 0 ? (uint32_t)std::min<int64_t>(P->wait_polls, 0xffffffffll) : WAIT_LIMIT;
   A.probe = P->probe_timeout;
   A.natural = P->schedule == 1;
+  {  // 2^(e-1) <= c + 6/h^2 < 2^e
+    int e = 0;
+    std::frexp(std::fabs(P->c) + 6.0 / (P->band->h * P->band->h), &e);
+    A.xsigma = (float)std::ldexp(1.0, std::max(-100, std::min(100, e - 1)));
+  }
   const size_t ring = (size_t)NSTAGE * CHUNK_BYTES + A.csz_bytes;
   const size_t xsb = (size_t)P->max_rows * sizeof(T);
   // local vector in shared memory when it fits beside the ring with two CTAs
