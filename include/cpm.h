@@ -140,7 +140,10 @@ cpm_status cpm_apply_noalloc(const cpm_band* band, const double* c, const void* 
 /* ------------------------------------------------------------------ Schwarz preconditioner
  * (Section 2.2; defaults of Section 4.1.1: alpha = 4, alpha_cross = 20, ILU(0) local solves)
  *   nparts       number of disjoint subdomains N_S, from recursive coordinate
- *                bisection of Sigma_A by lattice planes
+ *                bisection of Sigma_A by lattice planes; an overlapping
+ *                subdomain may hold at most 65,535 rows (the packed factors
+ *                carry 16-bit local columns): oras_setup returns CPM_ERR_ARG
+ *                beyond that, and a larger nparts is the remedy
  *   overlap      N_O: layers of 6-adjacency within Sigma_A added to each part
  *   robin        0: RAS (Dirichlet transmission); 1: ORAS with the Robin reading
  *                A_j[i,i] += D_i / (1 + alpha h), D_i the sum of the entries of
