@@ -71,6 +71,22 @@ def test_batch_problem_draws():
     assert len({round(p["h"], 6) for p in a}) >= 4
 
 
+def test_bench_local_vector_placement_override():
+    """The headline workload holds its Schwarz local vectors in FP16 in shared
+    memory (oras_tuning.xplace 3); --xplace replaces that for any workload."""
+    import bench
+    try:
+        assert bench.workload("torus_h0.002")["xplace"] == 3
+        assert "xplace" not in bench.workload("torus_h0.004")
+        args = bench.parse(["--xplace", "0"])
+        bench._XPLACE = args.xplace
+        assert bench.workload("torus_h0.002")["xplace"] == 0
+        assert bench.workload("torus_h0.004")["xplace"] == 0
+        assert bench.parse([]).xplace is None
+    finally:
+        bench._XPLACE = None
+
+
 def test_schnakenberg_initial_state():
     import bench
     w = inputs.WORKLOADS["schnakenberg_torus_h0.005"]
