@@ -8,15 +8,17 @@ c = 10, f = 20 random Fourier modes in the torus angles.  One step is
 
   band build (Sigma_A, Sigma_G, E rows)  ->  Schwarz set-up (512 parts,
   overlap 2, ILU(0))  ->  mixed-precision solve M u = f (FP32 operator and
-  Schwarz applies inside FP64 iterative refinement) to the relative residual
-  that keeps the error within 1e-8 of the FP64 solution.
+  Schwarz applies inside FP64 iterative refinement; the sweeps hold their
+  local vectors in FP16 in shared memory) to the relative residual that keeps
+  the error within 1e-8 of the FP64 solution.
 
 Reported value: band-point iterations per second of the whole step (N_A times
 the GMRES iterations divided by the step time), with inputs resident in HBM;
 `solves_per_s` beside it.  Outside the timed region: the plain FP64 GPU solve
 of the same system (speed-up and iterations), an FP64 reference solution at a
-tight tolerance (the stated errors of both solutions), the BF16 factor-storage
-ablation, the sphere case h = 0.1 (microseconds per iteration), the forward +
+tight tolerance (the stated errors of both solutions), the same solve with FP32
+local vectors (the apply autotuner's pick), the BF16 factor-storage ablation,
+the two-level preconditioner at 512 and 2048 parts, the sphere case h = 0.1 (microseconds per iteration), the forward +
 adjoint pipeline at h = 0.004, end to end through host buffers, the roofline of
 the dominant kernel from a separately instrumented solve, and the FP64 CPU
 oracle on a bounded sample of the same workload on one core and on all cores.
