@@ -206,6 +206,25 @@ def test_band_count_scales_like_the_papers_counts(oracle_mod):
     assert abs(vals[2] / vals[1] - 1) < 0.01
 
 
+@pytest.mark.parametrize("kind,prm,h,p", [(0, (0.0, 0.0, 0.0, 1.0), 0.1, 3), (1, (0.0, 0.0, 0.0, 1.0, 0.4), 0.05, 3),
+                                           (0, (0.013, 0.1, -0.07, 0.7), 0.03, 2)])
+def test_erow_cubes_lie_near_their_rows(oracle_mod, kind, prm, h, p):
+    """Every E row's interpolation cube lies within 6 cells of the row per
+    axis: active nodes are cube nodes, within 2 cells of a closest point per
+    axis (so within 2 sqrt(3) h of S), ghosts one cell further (4.46 h), and a
+    row's cube spans its closest point +-2 cells.  The FP32 apply that stages x
+    by 16^3 bricks relies on this: a brick's box (its nodes and the cubes of
+    the rows they need) spans at most 16 + 2 + 12 = 30 cells per axis."""
+    B = oracle_mod.Band(kind, prm, h, p)
+    A, G, base, cp = B.export()
+    rows = np.concatenate([A, G])
+    assert (base - rows).min() >= -6
+    assert (base + p - rows).max() <= 6
+    # the rows lie within 2 sqrt(3) h + h of the surface
+    d = np.linalg.norm(cp / h - rows, axis=1)
+    assert d.max() <= 2.0 * math.sqrt(3.0) + 1.0 + 1e-9
+
+
 def test_reach_violation_is_rejected(oracle_mod):
     with pytest.raises(oracle_mod.BandError) as e:
         oracle_mod.Band(1, (0, 0, 0, 1.0, 0.2), 0.05, 3)  # lambda = 0.206 > r
