@@ -21,8 +21,8 @@
 //   3. forms the stencil of each active node from that grid and writes y.
 // No intermediate goes through HBM and no gather needs a bitmap lookup.  The
 // contraction order of a row and the stencil's sum order are those of the
-// two-pass FP32 apply.  Rows that neighbour two bricks are evaluated by both (about
-// a fifth more rows than N_C at TB = 16).
+// two-pass FP32 apply.  Rows that neighbour two bricks are evaluated by both (1.2-1.3
+// records per E row at TB = 16 on the benchmark surfaces).
 //
 // Set-up (band build): bricks holding active nodes are listed in canonical
 // brick order; each marks the grid slots of the rows its nodes need; one CTA
