@@ -27,6 +27,7 @@ Other modes:
   --workload torus_h0.004   the same line at h = 0.004 (5.7M points)
   --workload batch          many uneven problems in one cpm_solve_batch call
                             against the same systems solved one by one
+                            (--coarse --restart 100: two-level Schwarz)
   --workload schnakenberg   differentiable Schnakenberg run (eq. schnack): forward
                             steps and the checkpointed adjoint gradient
   --profile KIND            a bare loop for ncu (no clocks, no oracle): `op`, `opT`
@@ -90,6 +91,10 @@ def parse(argv=None):
     ap.add_argument("--maxit", type=int, default=50000, help="--profile pipeline: iteration cap of each solve")
     ap.add_argument("--problems", type=int, default=96, help="--workload batch: number of problems")
     ap.add_argument("--hs", default="0.05,0.025,0.0125,0.00625", help="--workload batch: grid spacings")
+    ap.add_argument("--coarse", action="store_true",
+                    help="--workload batch: two-level Schwarz (with GMRES(30) it stalls on some small-shift "
+                         "draws; pair it with --restart 100)")
+    ap.add_argument("--restart", type=int, default=30, help="--workload batch: GMRES restart length")
     ap.add_argument("--fd-steps", type=int, default=0,
                     help="--workload schnakenberg: also check dL/dD_u, dL/dD_v of a run of this many steps "
                          "against central differences (solves at --rtol)")
@@ -595,7 +600,7 @@ def run_batch(args):
         B = cpm.Band(sp["kind"], sp["params"], sp["h"], 3)
         # one-level preconditioner (the two-level one stalls on some small-shift draws), apply settings
         # by the autotuner
-        P = cpm.Schwarz(B, sp["c"], max(1, int(round(B.n_active * 1.15 / rows))), 2)
+        P = cpm.Schwarz(B, sp["c"], max(1, int(round(B.n_active * 1.15 / rows))), 2, coarse=args.coarse)
         P.autotune(cpm.CPM_F32, reps=2)
         F = np.stack([inputs.gaussian_vector(sp["seed"] + r, B.n_active) for r in range(sp["nrhs"])])
         probs.append((B, P, sp["c"]))
@@ -605,7 +610,7 @@ def run_batch(args):
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t0
     _progress(f"batch: set-up of {len(probs)} problems {t_setup:.1f} s")
-    opts = dict(rtol=1e-8, maxit=100000, mixed=True)
+    opts = dict(rtol=1e-8, maxit=100000, mixed=True, restart=args.restart)
     cpm.solve_batch(probs[:2], rhs[:2], **opts)
     L0 = cpm.cpm_kernel_launches()
     (res, t_batch) = _timed(torch, lambda: cpm.solve_batch(probs, rhs, **opts))
@@ -637,8 +642,8 @@ def run_batch(args):
                                    f"unknowns, spacings {hs}, "
                                    f"{min(int(b.n_active) for b, _, _ in probs)}-"
                                    f"{max(int(b.n_active) for b, _, _ in probs)} band points, c log-uniform "
-                                   "0.1-1000, 1-8 right-hand sides, one-level Schwarz (autotuned apply), "
-                                   "mixed FP32/FP64 to 1e-8, CUDA-graph cycles"},
+                                   f"0.1-1000, 1-8 right-hand sides, {'two' if args.coarse else 'one'}-level Schwarz (autotuned apply), "
+                                   f"GMRES({args.restart}), mixed FP32/FP64 to 1e-8, CUDA-graph cycles"},
             "setup_s": t_setup, "batch_s": t_batch, "band_pt_iters_per_s": pt_iters / t_batch,
             "subset": {"problems": len(sub), "systems": sum(int(rhs[k].shape[0]) for k in sub),
                        "batch_s": t_bsub, "single_s": t_single, "batch_speedup": t_single / t_bsub},
